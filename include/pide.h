@@ -1,0 +1,217 @@
+/*
+ * pide.h -- C ABI of the GB300 dense-inverse Poisson apply.
+ *
+ * The method (Dourbal & Pekker, "A New Numerical Method for Fast Solution of
+ * Partial Integro-Differential Equations"): assemble the 5-point system of
+ * Eq. (2)/(3) on an nx x ny node grid (Fig. 3: boundary nodes are identity
+ * rows), invert it once ("The solution steps", step 2), then obtain every
+ * solution by one matrix-vector product with the inverse (step 3):
+ *
+ *     u = L_eps^-1 b          for many right-hand sides b at once.
+ *
+ * Notation used throughout.
+ *   Grid: nodes (i, j), 0 <= i < ny (y), 0 <= j < nx (x), spacing h in both
+ *     directions (Eq. 2).  Interior nodes 1 <= i <= ny-2, 1 <= j <= nx-2;
+ *     n = (nx-2)*(ny-2) unknowns, ordered as in Fig. 3 restricted to the
+ *     interior: index (i-1)*(nx-2) + (j-1), j fastest.
+ *   Operator (Eq. 3): row p reads u_p - sum_q w_pq u_q = b_p, with face
+ *     permittivity eps_pq = harmonic mean of the two node values and
+ *     w_pq = eps_pq / d_p, d_p = sum of the four face values of node p.  At
+ *     eps = 1 every w is 0.25 (Fig. 3).  Equivalently S u = D b with
+ *     D = diag(d), S = D L symmetric positive definite.
+ *   Right-hand side: b is the Eq. (3) right side at interior nodes.  From a
+ *     charge density (Eq. 1) it is b = -h^2 rho / d (pide_rhs_from_charge).
+ *   Boundary values: zero unless a boundary array g is given.
+ *
+ * Conventions.
+ *   - Every *_dev pointer is CUDA device memory owned by the caller, laid out
+ *     [B][n] (one right-hand side per row, row stride n), float64 unless stated.
+ *   - The handle owns the inverse, its quantised copy, scales and workspace.
+ *   - All work is ordered on the given cudaStream_t (passed as void*; NULL =
+ *     the legacy default stream).  Calls return after enqueueing unless an
+ *     output lives on the host (pide_info, pide_apply_host, pide_save).
+ *   - No call throws; each returns a pide_status.  pide_last_error() returns
+ *     a message for the last failure on the calling thread.
+ *   - One handle may be used from one host thread at a time.
+ */
+#ifndef PIDE_H
+#define PIDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pide_ctx* pide_handle;
+
+typedef enum {
+  PIDE_OK = 0,
+  PIDE_EINVAL = 1,       /* bad argument (size, NULL pointer, eps <= 0, NaN) */
+  PIDE_ENOMEM = 2,       /* device or host allocation failed */
+  PIDE_ECUDA = 3,        /* a CUDA runtime or driver call failed */
+  PIDE_ENOTCONV = 4,     /* tol not reached within max_sweeps (u is written) */
+  PIDE_ETIMEOUT = 5,     /* a bounded device-side wait gave up (kernel returned) */
+  PIDE_EUNSUPPORTED = 6  /* valid request this build cannot serve */
+} pide_status;
+
+/* Storage/contraction format of the inverse (step 2's result). */
+typedef enum {
+  PIDE_FP64 = 0,   /* plain FP64 inverse, FP64 apply (the comparator) */
+  PIDE_FP32 = 1,   /* FP32 inverse, FP32 SIMT apply, FP64 refinement */
+  PIDE_BF16 = 2,   /* BF16 inverse, tensor-core apply (FP32 accumulate), FP64 refinement */
+  PIDE_FP8 = 3,    /* e4m3 inverse with per-row scales (single term; study only) */
+  PIDE_FP8X2 = 4   /* e4m3 hi + lo terms with per-row scales, FP8 tensor cores */
+} pide_precision;
+
+typedef struct {
+  int32_t nx;      /* nodes along x including the two boundary nodes, >= 3 */
+  int32_t ny;      /* nodes along y including the two boundary nodes, >= 3 */
+  double h;        /* grid spacing (Eq. 2), > 0 */
+} pide_grid;
+
+typedef struct {
+  int32_t sweeps;        /* refinement sweeps executed */
+  int32_t converged;     /* 1 if tol was met (always 1 when tol <= 0) */
+  double rel_residual;   /* max over columns of ||b - L u||_inf / ||b||_inf (FP64) */
+  double setup_ms;       /* wall time of pide_setup for this handle */
+} pide_info;
+
+typedef struct {
+  int32_t n;             /* unknowns */
+  int32_t ld;            /* row stride (elements) of the stored inverse */
+  int32_t precision;     /* pide_precision */
+  int32_t num_sms;       /* SMs of the device the handle lives on */
+  size_t store_bytes;    /* bytes of the stored inverse (+ scales) read per apply */
+  double setup_ms;
+} pide_handle_info;
+
+/* Per-kernel-class event timing, recorded on the launching stream. */
+typedef struct {
+  int32_t launches[4];   /* [0] apply (GEMM/GEMV) [1] residual [2] rhs prep [3] other */
+  double ms[4];          /* summed CUDA-event time per class */
+} pide_profile;
+
+/*
+ * pide_setup -- steps 1 and 2: assemble the operator (Eq. 2/3, Fig. 3) from
+ * node permittivity and form its inverse.
+ *   g         grid (nx, ny >= 3, h > 0).
+ *   eps_host  [ny][nx] float64 node permittivity on the HOST, every value
+ *             finite and > 0 (NULL means eps = 1, the case of Eq. 2).
+ *   p         storage format of the inverse.  The inverse is always formed
+ *             in FP64 on the GPU (block-tridiagonal elimination), then
+ *             quantised; the FP64 copy is kept only for PIDE_FP64.
+ *   stream    cudaStream_t for all setup work (the call synchronises it).
+ *   out       receives the new handle (NULL on failure).
+ * Errors: EINVAL (bad grid, eps), ENOMEM, ECUDA, EUNSUPPORTED (no sm_100+).
+ */
+pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
+                       void* stream, pide_handle* out);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void pide_destroy(pide_handle h);
+
+/*
+ * pide_apply -- step 3 with iterative refinement:
+ *   u = Q(L^-1) b;  then up to max_sweeps times  u += Q(L^-1) (b - L u),
+ * where Q(.) is the stored inverse and the residual b - L u is taken in FP64
+ * with the 5-point stencil of Eq. (3).
+ *   b_dev     [B][n] right-hand sides (Eq. 3 form, interior nodes).
+ *   u_dev     [B][n] solutions (written; must not alias b_dev).
+ *   B         number of right-hand sides, >= 0 (0 is a no-op).
+ *   max_sweeps  refinement sweeps (0 = a single apply).
+ *   tol       > 0: stop early once ||b - L u||_inf <= tol ||b||_inf for every
+ *             column (checked on the device; later kernels return at once);
+ *             <= 0: run exactly max_sweeps sweeps.
+ *   g_dev     [ny][nx] boundary values on the device, or NULL for zero.
+ *   info      if non-NULL the call synchronises the stream and fills it.
+ * Errors: EINVAL, ENOMEM (workspace), ECUDA, ETIMEOUT, ENOTCONV (only when
+ * info is non-NULL and tol > 0 was not reached; u is still written).
+ */
+pide_status pide_apply(pide_handle h, const double* b_dev, double* u_dev, int32_t B,
+                       int32_t max_sweeps, double tol, const double* g_dev,
+                       void* stream, pide_info* info);
+
+/*
+ * pide_apply_host -- pide_apply on HOST buffers: copies b to the device,
+ * applies, copies u back and synchronises.  b_host/u_host are [B][n] float64
+ * (pinned memory makes the copies asynchronous-capable and fast).
+ */
+pide_status pide_apply_host(pide_handle h, const double* b_host, double* u_host, int32_t B,
+                            int32_t max_sweeps, double tol, void* stream, pide_info* info);
+
+/*
+ * pide_residual -- r = b - L u at interior nodes (Eq. 3 as a matrix-free
+ * 5-point stencil, FP64, zero boundary values).  b, u, r are [B][n]; r may
+ * alias neither b nor u.
+ */
+pide_status pide_residual(pide_handle h, const double* b_dev, const double* u_dev,
+                          double* r_dev, int32_t B, void* stream);
+
+/*
+ * pide_rhs_from_charge -- b = -h^2 rho / d: the Eq. (3) right side for a
+ * charge density rho of Eq. (1) (flux form; at eps = 1 this is -h^2 rho / 4).
+ * rho, b are [B][n]; b may alias rho.
+ */
+pide_status pide_rhs_from_charge(pide_handle h, const double* rho_dev, double* b_dev,
+                                 int32_t B, void* stream);
+
+/*
+ * pide_apply_backward -- adjoint of u = L(eps)^-1 b (b held fixed).  Given
+ * gout = dLoss/du, with mu = S^-1 gout (solved with the same stored inverse
+ * and FP64 refinement):
+ *   db   = dLoss/db = D mu                                   [B][n]
+ *   deps = dLoss/deps (node permittivity, [ny][nx]), ACCUMULATED into deps_dev:
+ *          per face f = (p,q): sum over columns of
+ *          mu_p b_p + mu_q b_q - (mu_p - mu_q)(u_p - u_q)  (boundary node: mu = 0,
+ *          no b term, u = 0), chained through the harmonic mean
+ *          d eps_f / d eps_a = 2 eps_b^2 / (eps_a + eps_b)^2.
+ * u_dev must be the forward solution for b_dev.  db_dev or deps_dev may be NULL.
+ * Not in the paper: the gradient follows from differentiating L u = b.
+ */
+pide_status pide_apply_backward(pide_handle h, const double* gout_dev, const double* u_dev,
+                                const double* b_dev, double* db_dev, double* deps_dev,
+                                int32_t B, int32_t max_sweeps, void* stream);
+
+/*
+ * pide_apply_batched -- pide_apply for nprob independent problems (handles
+ * of any grid size and format FP32/BF16) with ragged column counts Bs[k], in
+ * ONE persistent launch per phase (apply, residual) over a device work list
+ * of (problem, row tile) items.  b[k], u[k] are device pointers [Bs[k]][n_k].
+ * All handles must live on the current device.  sweeps as in pide_apply
+ * (fixed count, tol not supported).
+ */
+pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob, const double* const* b,
+                               double* const* u, const int32_t* Bs, int32_t sweeps,
+                               void* stream);
+
+/* Reserve workspace for up to Bmax columns now, so later pide_apply calls with
+ * B <= Bmax allocate nothing (required before capturing them in a CUDA graph). */
+pide_status pide_reserve(pide_handle h, int32_t Bmax);
+
+/* Persist / restore the stored inverse (+ scales) with a header of grid,
+ * format and an FNV-1a hash of eps; pide_load rebuilds the operator from the
+ * saved eps and skips step 2. */
+pide_status pide_save(pide_handle h, const char* path);
+pide_status pide_load(const char* path, void* stream, pide_handle* out);
+
+pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out);
+
+/* Event timing of every kernel the handle launches between begin and end
+ * (end synchronises the stream).  Off unless begun. */
+pide_status pide_profile_begin(pide_handle h);
+pide_status pide_profile_end(pide_handle h, pide_profile* out);
+
+/* Copy the stored inverse's row p (converted to float64, scales applied) to
+ * host memory dst[n]: lets tests check individual entries. */
+pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
+
+const char* pide_status_string(pide_status s);
+const char* pide_last_error(void);
+int32_t pide_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIDE_H */

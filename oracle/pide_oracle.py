@@ -471,3 +471,27 @@ def adjoint_gradients(nx: int, ny: int, eps: np.ndarray, b: np.ndarray,
         deps[ia, ja] += tot * 2 * eb * eb / (ea + eb) ** 2
         deps[ib, jb] += tot * 2 * ea * ea / (ea + eb) ** 2
     return u, db, deps
+
+
+# ---------------------------------------------------------------------------
+# Binary rounding of the stored inverse (the GPU's analogue of Table 1's
+# decimal rounding): round to nearest, ties to even, from float64.
+# ---------------------------------------------------------------------------
+
+
+def round_to_bits(x: np.ndarray, bits: int) -> np.ndarray:
+    """Round each value to ``bits`` significant bits (nearest, ties to even),
+    no exponent limit: x = m 2^e with 0.5 <= |m| < 1, m rounded to bits bits."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 2.0 ** bits) / 2.0 ** bits, e)
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """bfloat16 value of each entry (8 significant bits; normal range only)."""
+    return round_to_bits(x, 8)
+
+
+def round_fp32(x: np.ndarray) -> np.ndarray:
+    """float32 value of each entry (24 significant bits; normal range only)."""
+    return round_to_bits(x, 24)

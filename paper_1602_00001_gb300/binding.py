@@ -1,0 +1,329 @@
+"""Thin Python binding of libpide (include/pide.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; torch is used for
+device memory, streams and autograd plumbing.  There is no CPU fallback: if
+the library is missing or the GPU is not a GB300, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from contextlib import contextmanager
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpide.so")
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8x2": 4}
+STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
+          6: "EUNSUPPORTED"}
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double)]
+
+
+class HandleInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("ld", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("num_sms", ctypes.c_int32), ("store_bytes", ctypes.c_size_t),
+                ("setup_ms", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32 * 4), ("ms", ctypes.c_double * 4)]
+
+
+class PideError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_D = ctypes.c_double
+_SIGS = {
+    "pide_setup": (_I, [ctypes.POINTER(Grid), _P, _I, _P, ctypes.POINTER(_P)]),
+    "pide_destroy": (None, [_P]),
+    "pide_apply": (_I, [_P, _P, _P, _I, _I, _D, _P, _P, ctypes.POINTER(Info)]),
+    "pide_apply_host": (_I, [_P, _P, _P, _I, _I, _D, _P, ctypes.POINTER(Info)]),
+    "pide_residual": (_I, [_P, _P, _P, _P, _I, _P]),
+    "pide_rhs_from_charge": (_I, [_P, _P, _P, _I, _P]),
+    "pide_apply_backward": (_I, [_P, _P, _P, _P, _P, _P, _I, _I, _P]),
+    "pide_apply_batched": (_I, [_P, _I, _P, _P, _P, _I, _P]),
+    "pide_reserve": (_I, [_P, _I]),
+    "pide_save": (_I, [_P, ctypes.c_char_p]),
+    "pide_load": (_I, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
+    "pide_get_handle_info": (_I, [_P, ctypes.POINTER(HandleInfo)]),
+    "pide_profile_begin": (_I, [_P]),
+    "pide_profile_end": (_I, [_P, ctypes.POINTER(Profile)]),
+    "pide_get_inverse_row": (_I, [_P, _I, _P]),
+    "pide_status_string": (ctypes.c_char_p, [_I]),
+    "pide_last_error": (ctypes.c_char_p, []),
+    "pide_version": (_I, []),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpide.so (build it first with ``build.build()``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpide.so not found at {path}: run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = _LIB.pide_last_error().decode(errors="replace")
+        raise PideError(status, f"{what}: {msg}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _as_dev(x, device):
+    import torch
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    x = x.to(device=device, dtype=torch.float64)
+    return x.contiguous()
+
+
+class Solver:
+    """One operator (grid + node permittivity) with its stored inverse.
+
+    ``precision``: 'fp64' (plain FP64 inverse and apply), 'fp32', 'bf16',
+    'fp8' or 'fp8x2' (low-precision inverse, FP64 refinement).
+    """
+
+    def __init__(self, nx: int, ny: int, h: float, eps=None, precision: str = "bf16",
+                 stream=None, _handle=None):
+        import torch
+        self.lib = load_library()
+        self.nx, self.ny, self.h = int(nx), int(ny), float(h)
+        self.n = (self.nx - 2) * (self.ny - 2)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if _handle is not None:
+            self.handle = _handle
+        else:
+            g = Grid(self.nx, self.ny, self.h)
+            eps_p = None
+            self._eps_keep = None
+            if eps is not None:
+                e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(self.ny, self.nx))
+                self._eps_keep = e
+                eps_p = e.ctypes.data_as(ctypes.c_void_p)
+            h_out = ctypes.c_void_p()
+            _check(self.lib.pide_setup(ctypes.byref(g), eps_p, PRECISIONS[precision],
+                                       _stream(stream), ctypes.byref(h_out)), "pide_setup")
+            self.handle = h_out
+        self.eps = None if eps is None else np.asarray(eps, dtype=np.float64).reshape(self.ny, self.nx)
+
+    # -- life cycle
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pide_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> HandleInfo:
+        out = HandleInfo()
+        _check(self.lib.pide_get_handle_info(self.handle, ctypes.byref(out)), "pide_get_handle_info")
+        return out
+
+    # -- step 3 with refinement
+    def apply(self, b, u=None, sweeps: int = 0, tol: float = 0.0, g=None, stream=None,
+              want_info: bool = False):
+        import torch
+        b = _as_dev(b, self.device)
+        b2 = b.reshape(-1, self.n)
+        B = b2.shape[0]
+        if u is None:
+            u = torch.empty_like(b2)
+        gd = _as_dev(g, self.device) if g is not None else None
+        info = Info()
+        _check(self.lib.pide_apply(self.handle, _ptr(b2), _ptr(u), B, int(sweeps), float(tol),
+                                   _ptr(gd), _stream(stream),
+                                   ctypes.byref(info) if want_info else None), "pide_apply")
+        return (u, info) if want_info else u
+
+    def apply_host(self, b_host: np.ndarray, u_host: np.ndarray | None = None, sweeps: int = 0,
+                   tol: float = 0.0, stream=None, want_info: bool = False):
+        """Host buffers in and out (numpy float64 [B][n], or pinned torch CPU tensors)."""
+        import torch
+        if isinstance(b_host, torch.Tensor):
+            bptr, B = b_host.data_ptr(), b_host.reshape(-1, self.n).shape[0]
+            if u_host is None:
+                u_host = torch.empty_like(b_host)
+            uptr = u_host.data_ptr()
+        else:
+            b_host = np.ascontiguousarray(b_host, dtype=np.float64).reshape(-1, self.n)
+            B = b_host.shape[0]
+            if u_host is None:
+                u_host = np.empty_like(b_host)
+            bptr, uptr = b_host.ctypes.data, u_host.ctypes.data
+        info = Info()
+        _check(self.lib.pide_apply_host(self.handle, ctypes.c_void_p(bptr), ctypes.c_void_p(uptr),
+                                        B, int(sweeps), float(tol), _stream(stream),
+                                        ctypes.byref(info) if want_info else None),
+               "pide_apply_host")
+        return (u_host, info) if want_info else u_host
+
+    def residual(self, b, u, stream=None):
+        import torch
+        b = _as_dev(b, self.device).reshape(-1, self.n)
+        u = _as_dev(u, self.device).reshape(-1, self.n)
+        r = torch.empty_like(b)
+        _check(self.lib.pide_residual(self.handle, _ptr(b), _ptr(u), _ptr(r), b.shape[0],
+                                      _stream(stream)), "pide_residual")
+        return r
+
+    def rhs_from_charge(self, rho, stream=None):
+        import torch
+        rho = _as_dev(rho, self.device).reshape(-1, self.n)
+        b = torch.empty_like(rho)
+        _check(self.lib.pide_rhs_from_charge(self.handle, _ptr(rho), _ptr(b), rho.shape[0],
+                                             _stream(stream)), "pide_rhs_from_charge")
+        return b
+
+    def backward(self, gout, u, b, sweeps: int = 4, stream=None):
+        """(dLoss/db, dLoss/deps) for u = L(eps)^-1 b given gout = dLoss/du."""
+        import torch
+        gout = _as_dev(gout, self.device).reshape(-1, self.n)
+        u = _as_dev(u, self.device).reshape(-1, self.n)
+        b = _as_dev(b, self.device).reshape(-1, self.n)
+        db = torch.empty_like(gout)
+        deps = torch.zeros((self.ny, self.nx), dtype=torch.float64, device=self.device)
+        _check(self.lib.pide_apply_backward(self.handle, _ptr(gout), _ptr(u), _ptr(b), _ptr(db),
+                                            _ptr(deps), gout.shape[0], int(sweeps),
+                                            _stream(stream)), "pide_apply_backward")
+        return db, deps
+
+    def reserve(self, Bmax: int):
+        _check(self.lib.pide_reserve(self.handle, int(Bmax)), "pide_reserve")
+
+    def inverse_row(self, p: int) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.float64)
+        _check(self.lib.pide_get_inverse_row(self.handle, int(p),
+                                             out.ctypes.data_as(ctypes.c_void_p)),
+               "pide_get_inverse_row")
+        return out
+
+    def save(self, path: str):
+        _check(self.lib.pide_save(self.handle, path.encode()), "pide_save")
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Solver":
+        lib = load_library()
+        h_out = ctypes.c_void_p()
+        _check(lib.pide_load(path.encode(), _stream(stream), ctypes.byref(h_out)), "pide_load")
+        hi = HandleInfo()
+        _check(lib.pide_get_handle_info(h_out, ctypes.byref(hi)), "pide_get_handle_info")
+        inv = {v: k for k, v in PRECISIONS.items()}
+        # grid shape is in the file header; read it back from the header bytes
+        import struct
+        with open(path, "rb") as f:
+            head = f.read(8 + 4 * 6 + 8)
+        _, _, nx, ny, prec, n, ld = struct.unpack("<8s6i", head[:32])
+        (h,) = struct.unpack("<d", head[32:40])
+        return cls(nx, ny, h, None, inv[hi.precision], _handle=h_out)
+
+    @contextmanager
+    def profile(self):
+        """Event-time every kernel launched inside the block; yields a dict
+        filled at exit: {'apply': (launches, ms), 'residual': ..., 'prep': ..., 'other': ...}."""
+        out: dict = {}
+        _check(self.lib.pide_profile_begin(self.handle), "pide_profile_begin")
+        try:
+            yield out
+        finally:
+            p = Profile()
+            _check(self.lib.pide_profile_end(self.handle, ctypes.byref(p)), "pide_profile_end")
+            for i, name in enumerate(["apply", "residual", "prep", "other"]):
+                out[name] = (int(p.launches[i]), float(p.ms[i]))
+
+
+def apply_batched(solvers, bs, us, sweeps: int = 2, stream=None):
+    """pide_apply_batched over several solvers (uneven grids, ragged B)."""
+    lib = load_library()
+    k = len(solvers)
+    hs = (ctypes.c_void_p * k)(*[s.handle.value for s in solvers])
+    bp = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
+    up = (ctypes.c_void_p * k)(*[u.data_ptr() for u in us])
+    Bs = (ctypes.c_int32 * k)(*[b.reshape(-1, s.n).shape[0] for b, s in zip(bs, solvers)])
+    _check(lib.pide_apply_batched(hs, k, bp, up, Bs, int(sweeps), _stream(stream)),
+           "pide_apply_batched")
+
+
+def header_symbols(header: str | None = None):
+    """Names of the functions include/pide.h declares."""
+    import re
+    header = header or os.path.join(HERE, "..", "include", "pide.h")
+    text = open(header).read()
+    return sorted(set(re.findall(r"\b(pide_[a-z_0-9]+)\s*\(", text)))
+
+
+def _autograd():
+    import torch
+
+    class PideApply(torch.autograd.Function):
+        """u = L(eps)^-1 b with the refined apply; backward through the adjoint
+        kernels (dLoss/db = D mu, dLoss/deps via the face gradient)."""
+
+        @staticmethod
+        def forward(ctx, b, eps, solver, sweeps):
+            u = solver.apply(b, sweeps=sweeps)
+            ctx.solver, ctx.sweeps = solver, sweeps
+            ctx.save_for_backward(b, u)
+            return u.reshape(b.shape)
+
+        @staticmethod
+        def backward(ctx, gout):
+            b, u = ctx.saved_tensors
+            db, deps = ctx.solver.backward(gout.contiguous(), u, b, sweeps=ctx.sweeps)
+            return db.reshape(b.shape), deps, None, None
+
+    return PideApply
+
+
+_PIDE_APPLY = None
+
+
+def pide_apply_autograd(b, eps_t, solver: Solver, sweeps: int = 4):
+    """Differentiable apply: gradients flow to b and to the node permittivity
+    tensor eps_t ([ny][nx], the values the solver was built with)."""
+    global _PIDE_APPLY
+    if _PIDE_APPLY is None:
+        _PIDE_APPLY = _autograd()
+    return _PIDE_APPLY.apply(b, eps_t, solver, sweeps)

@@ -1,0 +1,672 @@
+// C ABI of libpide (declared in include/pide.h): handle life cycle, the
+// refinement driver around the apply kernels, host-buffer apply, adjoint,
+// batched apply, persistence and profiling.
+#include <cudaTypedefs.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace pide {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+size_t rhs_elem_bytes(int rfmt) {
+  switch (rfmt) {
+    case RF_F64: return 8;
+    case RF_F32: return 4;
+    case RF_BF16: return 2;
+    default: return 1;
+  }
+}
+
+int rhs_format(const pide_ctx* c, int B) {
+  switch (c->prec) {
+    case PIDE_FP64: return RF_F64;
+    case PIDE_FP32: return RF_F32;
+    case PIDE_BF16: return B <= c->gemv_max_b ? RF_F32 : RF_BF16;
+    default: return B <= c->gemv_max_b ? RF_F32 : RF_E4M3;
+  }
+}
+
+ProfScope::ProfScope(pide_ctx* c_, cudaStream_t st_, int cls_) : c(c_), st(st_), cls(cls_) {
+  if (c && c->prof_on) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (a) {
+    cudaEventRecord(b, st);
+    c->prof_events.push_back({a, b, cls});
+  }
+}
+
+// ---------------------------------------------------------------- TMA maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+static pide_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base,
+                             uint64_t inner, uint64_t outer, uint64_t row_bytes, uint32_t box_in,
+                             uint32_t box_out) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return PIDE_EUNSUPPORTED;
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_in, box_out};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+    return PIDE_ECUDA;
+  }
+  return PIDE_OK;
+}
+
+pide_status make_tma_maps(pide_ctx* c) {
+  c->tmA_ok = false;
+  if (c->prec == PIDE_BF16) {
+    PIDE_TRY(encode_2d(&c->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c->inv, c->n, c->n,
+                       (uint64_t)c->ld * 2, 64, 128));
+  } else if (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2) {
+    PIDE_TRY(encode_2d(&c->tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->inv, c->n, c->n,
+                       (uint64_t)c->ld, 128, 128));
+    if (c->prec == PIDE_FP8X2)
+      PIDE_TRY(encode_2d(&c->tmA_lo, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->inv_lo, c->n, c->n,
+                         (uint64_t)c->ld, 128, 128));
+    else
+      c->tmA_lo = c->tmA;
+  } else {
+    return PIDE_OK;
+  }
+  c->tmA_ok = true;
+  return PIDE_OK;
+}
+
+pide_status make_tma_rhs(pide_ctx* c, int bn) {
+  if (c->prec == PIDE_BF16)
+    return encode_2d(&c->tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c->R, c->n, c->ws_B,
+                     (uint64_t)c->ld * 2, 64, bn);
+  return encode_2d(&c->tmR, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->R, c->n, c->ws_B, (uint64_t)c->ld,
+                   128, bn);
+}
+
+// ---------------------------------------------------------------- workspace
+
+pide_status ensure_workspace(pide_ctx* c, int B) {
+  if (B <= c->ws_B && c->R) return PIDE_OK;
+  int nb = B < 16 ? 16 : B;
+  if (c->R) cudaFree(c->R);
+  if (c->col_scale) cudaFree(c->col_scale);
+  if (c->colmax) cudaFree(c->colmax);
+  c->R = nullptr;
+  c->col_scale = nullptr;
+  c->colmax = nullptr;
+  c->ws_B = 0;
+  const size_t esz = c->prec == PIDE_FP64 ? 8 : 4;
+  PIDE_CUDA_TRY(cudaMalloc(&c->R, (size_t)nb * c->ld * esz));
+  PIDE_CUDA_TRY(cudaMemset(c->R, 0, (size_t)nb * c->ld * esz));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->col_scale, (size_t)nb * sizeof(float)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->colmax, 3 * (size_t)nb * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMemset(c->colmax, 0, 3 * (size_t)nb * sizeof(double)));
+  c->ws_B = nb;
+  return PIDE_OK;
+}
+
+// ---------------------------------------------------------------- apply
+
+pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+  if (B == 0) return PIDE_OK;
+  ProfScope ps(c, st, 0);
+  if (B <= c->gemv_max_b) return launch_gemv(c, B, u, accumulate, st);
+  if (c->prec == PIDE_FP64 || c->prec == PIDE_FP32) return launch_gemm_simt(c, B, u, accumulate, st);
+  return launch_gemm_tc(c, B, u, accumulate, st);
+}
+
+// S x = rhs~ with x = Q(S^-1) q(rhs~), then `sweeps` refinement sweeps
+// x += Q(S^-1) q(rhs~ - S x).  mode 0: rhs~ = D b + lift; mode 1: rhs~ = b.
+static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, double* x,
+                           int B, int sweeps, double tol, cudaStream_t st) {
+  PIDE_TRY(ensure_workspace(c, B));
+  PIDE_CUDA_TRY(cudaMemsetAsync(c->flags, 0, FLAG_COUNT * sizeof(uint32_t), st));
+  PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, 3 * (size_t)c->ws_B * sizeof(double), st));
+  const int rf = rhs_format(c, B);
+  if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
+  PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, st));
+  PIDE_TRY(launch_apply(c, B, x, false, st));
+  for (int k = 0; k < sweeps; ++k) {
+    if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, x, B, mode, lift, true, st));
+    PIDE_TRY(launch_residual(c, b, x, B, mode, lift, rf, true, nullptr, tol > 0, true, st));
+    if (tol > 0) PIDE_TRY(launch_check(c, B, tol, st));
+    PIDE_TRY(launch_apply(c, B, x, true, st));
+  }
+  return PIDE_OK;
+}
+
+static pide_status fill_info(pide_ctx* c, const double* b, const double* x, int B, int mode,
+                             const double* lift, int sweeps, double tol, cudaStream_t st,
+                             pide_info* info) {
+  // one more residual, tracked, ignoring the early-exit flag
+  PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, (size_t)c->ws_B * sizeof(double), st));
+  PIDE_TRY(launch_residual(c, b, x, B, mode, lift, RF_F64, false, nullptr, true, false, st));
+  std::vector<double> cm(2 * (size_t)c->ws_B);
+  uint32_t fl[FLAG_COUNT];
+  PIDE_CUDA_TRY(cudaMemcpyAsync(cm.data(), c->colmax, cm.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+  PIDE_CUDA_TRY(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+  PIDE_CUDA_TRY(cudaStreamSynchronize(st));
+  double worst = 0.0;
+  for (int k = 0; k < B; ++k) {
+    const double den = cm[c->ws_B + k];
+    const double r = den > 0 ? cm[k] / den : cm[k];
+    if (r > worst) worst = r;
+  }
+  info->rel_residual = worst;
+  info->setup_ms = c->setup_ms;
+  if (tol > 0) {
+    info->converged = worst <= tol ? 1 : 0;
+    info->sweeps = (int)fl[FLAG_SWEEPS];
+  } else {
+    info->converged = 1;
+    info->sweeps = sweeps;
+  }
+  if (fl[FLAG_ERROR]) {
+    set_error("device-side wait timed out (code " + std::to_string(fl[FLAG_ERROR]) + ")");
+    return PIDE_ETIMEOUT;
+  }
+  if (tol > 0 && !info->converged) {
+    set_error("tolerance not reached within max_sweeps");
+    return PIDE_ENOTCONV;
+  }
+  return PIDE_OK;
+}
+
+static pide_status check_device_error(pide_ctx* c, cudaStream_t st) {
+  uint32_t e = 0;
+  PIDE_CUDA_TRY(cudaMemcpyAsync(&e, c->flags + FLAG_ERROR, sizeof(e), cudaMemcpyDeviceToHost, st));
+  PIDE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (e) {
+    set_error("device-side wait timed out (code " + std::to_string(e) + ")");
+    return PIDE_ETIMEOUT;
+  }
+  return PIDE_OK;
+}
+
+}  // namespace pide
+
+using namespace pide;
+
+// ---------------------------------------------------------------- setup / destroy
+
+static bool valid_grid(const pide_grid* g) {
+  return g && g->nx >= 3 && g->ny >= 3 && std::isfinite(g->h) && g->h > 0 &&
+         (int64_t)(g->nx - 2) * (g->ny - 2) < (int64_t)1 << 30;
+}
+
+static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double* eps_host,
+                                  cudaStream_t st) {
+  c->nx = g->nx;
+  c->ny = g->ny;
+  c->h = g->h;
+  c->mx = g->nx - 2;
+  c->my = g->ny - 2;
+  c->n = c->mx * c->my;
+  c->ld = ((c->n + 63) / 64) * 64;
+  const size_t N = (size_t)c->nx * c->ny;
+  c->eps_host.assign(N, 1.0);
+  if (eps_host) {
+    for (size_t k = 0; k < N; ++k) {
+      if (!std::isfinite(eps_host[k]) || !(eps_host[k] > 0.0)) {
+        set_error("eps must be finite and > 0 at every node");
+        return PIDE_EINVAL;
+      }
+      c->eps_host[k] = eps_host[k];
+    }
+  }
+  PIDE_CUDA_TRY(cudaGetDevice(&c->device));
+  cudaDeviceProp prop;
+  PIDE_CUDA_TRY(cudaGetDeviceProperties(&prop, c->device));
+  if (prop.major != 10 || prop.minor != 3) {
+    set_error("this library is built for sm_103a (GB300); device is sm_" +
+              std::to_string(prop.major) + std::to_string(prop.minor));
+    return PIDE_EUNSUPPORTED;
+  }
+  c->num_sms = prop.multiProcessorCount;
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->eps, N * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->cf, 4 * (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->d, (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->lift, (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->flags, FLAG_COUNT * sizeof(uint32_t)));
+  PIDE_CUDA_TRY(cudaMemset(c->flags, 0, FLAG_COUNT * sizeof(uint32_t)));
+  PIDE_CUDA_TRY(cudaMemcpyAsync(c->eps, c->eps_host.data(), N * sizeof(double),
+                                cudaMemcpyHostToDevice, st));
+  PIDE_TRY(launch_assemble(c, st));
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
+                                  void* stream, pide_handle* out) {
+  if (out) *out = nullptr;
+  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 4) {
+    set_error("pide_setup: bad argument");
+    return PIDE_EINVAL;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  pide_ctx* c = new pide_ctx();
+  c->prec = p;
+  pide_status s = setup_operator(c, g, eps_host, st);
+  double* G = nullptr;
+  if (s == PIDE_OK) {
+    const size_t bytes = (size_t)c->n * c->ld * sizeof(double);
+    cudaError_t e = cudaMalloc((void**)&G, bytes);
+    if (e != cudaSuccess) {
+      set_error(std::string("allocating the FP64 inverse: ") + cudaGetErrorString(e));
+      s = e == cudaErrorMemoryAllocation ? PIDE_ENOMEM : PIDE_ECUDA;
+    } else if ((e = cudaMemsetAsync(G, 0, bytes, st)) != cudaSuccess) {
+      set_error(cudaGetErrorString(e));
+      s = PIDE_ECUDA;
+    }
+  }
+  if (s == PIDE_OK) s = build_inverse_fp64(c, G, st);
+  if (s == PIDE_OK) {
+    if (p == PIDE_FP64) {
+      c->inv = G;
+      c->store_bytes = (size_t)c->n * c->ld * sizeof(double);
+      G = nullptr;
+    } else {
+      s = quantize_store(c, G, st);
+    }
+  }
+  if (s == PIDE_OK) s = make_tma_maps(c);
+  if (s == PIDE_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error(std::string("setup kernels: ") + cudaGetErrorString(e));
+      s = PIDE_ECUDA;
+    }
+  }
+  if (G) cudaFree(G);
+  if (s != PIDE_OK) {
+    pide_destroy(c);
+    return s;
+  }
+  c->setup_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return PIDE_OK;
+}
+
+extern "C" void pide_destroy(pide_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  void* ptrs[] = {h->eps, h->cf, h->d, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
+                  h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& ev : h->prof_events) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  delete h;
+}
+
+// ---------------------------------------------------------------- apply entry points
+
+static pide_status check_apply_args(pide_handle h, const void* b, const void* u, int32_t B,
+                                    int32_t sweeps) {
+  if (!h || B < 0 || sweeps < 0 || (B > 0 && (!b || !u)) || (B > 0 && b == u) || B > 65535) {
+    set_error("bad argument (handle, pointers, B in [0, 65535], sweeps >= 0, b != u)");
+    return PIDE_EINVAL;
+  }
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_apply(pide_handle h, const double* b_dev, double* u_dev, int32_t B,
+                                  int32_t max_sweeps, double tol, const double* g_dev,
+                                  void* stream, pide_info* info) {
+  PIDE_TRY(check_apply_args(h, b_dev, u_dev, B, max_sweeps));
+  if (B == 0) {
+    if (info) *info = pide_info{0, 1, 0.0, h->setup_ms};
+    return PIDE_OK;
+  }
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* lift = nullptr;
+  if (g_dev) {
+    PIDE_TRY(launch_lift(h, g_dev, st));
+    lift = h->lift;
+  }
+  PIDE_TRY(solve_s(h, b_dev, 0, lift, u_dev, B, max_sweeps, tol, st));
+  if (info) return fill_info(h, b_dev, u_dev, B, 0, lift, max_sweeps, tol, st, info);
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_apply_host(pide_handle h, const double* b_host, double* u_host,
+                                       int32_t B, int32_t max_sweeps, double tol, void* stream,
+                                       pide_info* info) {
+  PIDE_TRY(check_apply_args(h, b_host, u_host, B, max_sweeps));
+  if (B == 0) return PIDE_OK;
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (B > h->hbuf_B) {
+    if (h->hbuf_b) cudaFree(h->hbuf_b);
+    if (h->hbuf_u) cudaFree(h->hbuf_u);
+    h->hbuf_b = h->hbuf_u = nullptr;
+    h->hbuf_B = 0;
+    PIDE_CUDA_TRY(cudaMalloc((void**)&h->hbuf_b, (size_t)B * h->n * sizeof(double)));
+    PIDE_CUDA_TRY(cudaMalloc((void**)&h->hbuf_u, (size_t)B * h->n * sizeof(double)));
+    h->hbuf_B = B;
+  }
+  const size_t bytes = (size_t)B * h->n * sizeof(double);
+  PIDE_CUDA_TRY(cudaMemcpyAsync(h->hbuf_b, b_host, bytes, cudaMemcpyHostToDevice, st));
+  PIDE_TRY(solve_s(h, h->hbuf_b, 0, nullptr, h->hbuf_u, B, max_sweeps, tol, st));
+  PIDE_CUDA_TRY(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, st));
+  if (info) return fill_info(h, h->hbuf_b, h->hbuf_u, B, 0, nullptr, max_sweeps, tol, st, info);
+  return check_device_error(h, st);
+}
+
+extern "C" pide_status pide_residual(pide_handle h, const double* b_dev, const double* u_dev,
+                                     double* r_dev, int32_t B, void* stream) {
+  if (!h || B < 0 || (B > 0 && (!b_dev || !u_dev || !r_dev)) || r_dev == b_dev || r_dev == u_dev) {
+    set_error("pide_residual: bad argument");
+    return PIDE_EINVAL;
+  }
+  if (B == 0) return PIDE_OK;
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  PIDE_TRY(ensure_workspace(h, B));
+  return launch_residual(h, b_dev, u_dev, B, 0, nullptr, RF_F64, false, r_dev, false, false,
+                         (cudaStream_t)stream);
+}
+
+extern "C" pide_status pide_rhs_from_charge(pide_handle h, const double* rho_dev, double* b_dev,
+                                            int32_t B, void* stream) {
+  if (!h || B < 0 || (B > 0 && (!rho_dev || !b_dev))) {
+    set_error("pide_rhs_from_charge: bad argument");
+    return PIDE_EINVAL;
+  }
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  return launch_rhs_from_charge(h, rho_dev, b_dev, B, (cudaStream_t)stream);
+}
+
+extern "C" pide_status pide_apply_backward(pide_handle h, const double* gout_dev,
+                                           const double* u_dev, const double* b_dev,
+                                           double* db_dev, double* deps_dev, int32_t B,
+                                           int32_t max_sweeps, void* stream) {
+  PIDE_TRY(check_apply_args(h, gout_dev, u_dev, B, max_sweeps));
+  if (B > 0 && (!b_dev)) {
+    set_error("pide_apply_backward: b_dev is required");
+    return PIDE_EINVAL;
+  }
+  if (B == 0) return PIDE_OK;
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  double* mu = nullptr;
+  PIDE_CUDA_TRY(cudaMallocAsync((void**)&mu, (size_t)B * h->n * sizeof(double), st));
+  pide_status s = solve_s(h, gout_dev, 1, nullptr, mu, B, max_sweeps, 0.0, st);
+  if (s == PIDE_OK && db_dev) s = launch_scale_d(h, mu, db_dev, B, st);
+  if (s == PIDE_OK && deps_dev) s = launch_face_grad(h, mu, u_dev, b_dev, B, deps_dev, st);
+  cudaFreeAsync(mu, st);
+  if (s != PIDE_OK) return s;
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_reserve(pide_handle h, int32_t Bmax) {
+  if (!h || Bmax < 0) {
+    set_error("pide_reserve: bad argument");
+    return PIDE_EINVAL;
+  }
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  return ensure_workspace(h, Bmax);
+}
+
+// ---------------------------------------------------------------- batched
+
+extern "C" pide_status pide_apply_batched_impl(const pide_handle* hs, int32_t nprob,
+                                               const double* const* b, double* const* u,
+                                               const int32_t* Bs, int32_t sweeps, void* stream);
+
+extern "C" pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob,
+                                          const double* const* b, double* const* u,
+                                          const int32_t* Bs, int32_t sweeps, void* stream) {
+  if (nprob < 0 || (nprob > 0 && (!hs || !b || !u || !Bs)) || sweeps < 0) {
+    set_error("pide_apply_batched: bad argument");
+    return PIDE_EINVAL;
+  }
+  for (int k = 0; k < nprob; ++k) PIDE_TRY(check_apply_args(hs[k], b[k], u[k], Bs[k], sweeps));
+  return pide_apply_batched_impl(hs, nprob, b, u, Bs, sweeps, stream);
+}
+
+// ---------------------------------------------------------------- persistence
+
+namespace {
+struct FileHeader {
+  char magic[8];
+  int32_t version, nx, ny, prec, n, ld;
+  double h;
+  uint64_t eps_hash;
+  uint64_t store_bytes;
+};
+
+uint64_t fnv1a(const void* data, size_t len) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  uint64_t hsh = 1469598103934665603ull;
+  for (size_t k = 0; k < len; ++k) {
+    hsh ^= p[k];
+    hsh *= 1099511628211ull;
+  }
+  return hsh;
+}
+}  // namespace
+
+extern "C" pide_status pide_save(pide_handle h, const char* path) {
+  if (!h || !path) {
+    set_error("pide_save: bad argument");
+    return PIDE_EINVAL;
+  }
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  PIDE_CUDA_TRY(cudaDeviceSynchronize());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("cannot open ") + path);
+    return PIDE_EINVAL;
+  }
+  const size_t main_bytes = (size_t)h->n * h->ld *
+                            (h->prec == PIDE_FP64 ? 8 : h->prec == PIDE_FP32 ? 4 : h->prec == PIDE_BF16 ? 2 : 1);
+  FileHeader hd{};
+  std::memcpy(hd.magic, "PIDEINV1", 8);
+  hd.version = 1;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.prec = (int)h->prec;
+  hd.n = h->n;
+  hd.ld = h->ld;
+  hd.h = h->h;
+  hd.eps_hash = fnv1a(h->eps_host.data(), h->eps_host.size() * sizeof(double));
+  hd.store_bytes = main_bytes;
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  ok = ok && std::fwrite(h->eps_host.data(), sizeof(double), h->eps_host.size(), f) == h->eps_host.size();
+  std::vector<char> buf(1 << 26);
+  auto dump = [&](const void* dev, size_t bytes) {
+    for (size_t off = 0; ok && off < bytes; off += buf.size()) {
+      const size_t len = std::min(buf.size(), bytes - off);
+      ok = cudaMemcpy(buf.data(), (const char*)dev + off, len, cudaMemcpyDeviceToHost) == cudaSuccess;
+      ok = ok && std::fwrite(buf.data(), 1, len, f) == len;
+    }
+  };
+  dump(h->inv, main_bytes);
+  if (h->inv_lo) dump(h->inv_lo, main_bytes);
+  if (h->row_scale) dump(h->row_scale, (size_t)h->n * sizeof(float));
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    set_error(std::string("writing ") + path + " failed");
+    return PIDE_ECUDA;
+  }
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* out) {
+  if (!path || !out) {
+    set_error("pide_load: bad argument");
+    return PIDE_EINVAL;
+  }
+  *out = nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("cannot open ") + path);
+    return PIDE_EINVAL;
+  }
+  FileHeader hd{};
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, "PIDEINV1", 8) == 0 &&
+            hd.version == 1;
+  pide_grid g{hd.nx, hd.ny, hd.h};
+  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 4) {
+    std::fclose(f);
+    set_error(std::string(path) + ": not a pide inverse file");
+    return PIDE_EINVAL;
+  }
+  std::vector<double> eps((size_t)hd.nx * hd.ny);
+  ok = std::fread(eps.data(), sizeof(double), eps.size(), f) == eps.size();
+  if (!ok || fnv1a(eps.data(), eps.size() * sizeof(double)) != hd.eps_hash) {
+    std::fclose(f);
+    set_error(std::string(path) + ": eps block corrupt (hash mismatch)");
+    return PIDE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  pide_ctx* c = new pide_ctx();
+  c->prec = (pide_precision)hd.prec;
+  pide_status s = setup_operator(c, &g, eps.data(), st);
+  if (s == PIDE_OK && (c->n != hd.n || c->ld != hd.ld)) {
+    set_error("pide_load: header sizes do not match the grid");
+    s = PIDE_EINVAL;
+  }
+  std::vector<char> buf(1 << 26);
+  auto load = [&](void** dev, size_t bytes) -> pide_status {
+    cudaError_t e = cudaMalloc(dev, bytes);
+    if (e != cudaSuccess) {
+      set_error(cudaGetErrorString(e));
+      return PIDE_ENOMEM;
+    }
+    for (size_t off = 0; off < bytes; off += buf.size()) {
+      const size_t len = std::min(buf.size(), bytes - off);
+      if (std::fread(buf.data(), 1, len, f) != len) {
+        set_error("pide_load: file truncated");
+        return PIDE_EINVAL;
+      }
+      if (cudaMemcpy((char*)*dev + off, buf.data(), len, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("pide_load: upload failed");
+        return PIDE_ECUDA;
+      }
+    }
+    return PIDE_OK;
+  };
+  if (s == PIDE_OK) s = load(&c->inv, hd.store_bytes);
+  if (s == PIDE_OK && c->prec == PIDE_FP8X2) s = load(&c->inv_lo, hd.store_bytes);
+  if (s == PIDE_OK && (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2))
+    s = load((void**)&c->row_scale, (size_t)c->n * sizeof(float));
+  std::fclose(f);
+  if (s == PIDE_OK) {
+    c->store_bytes = hd.store_bytes * (c->prec == PIDE_FP8X2 ? 2 : 1);
+    s = make_tma_maps(c);
+  }
+  if (s == PIDE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PIDE_ECUDA;
+  if (s != PIDE_OK) {
+    pide_destroy(c);
+    return s;
+  }
+  c->setup_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return PIDE_OK;
+}
+
+// ---------------------------------------------------------------- queries, profiling
+
+extern "C" pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out) {
+  if (!h || !out) {
+    set_error("pide_get_handle_info: bad argument");
+    return PIDE_EINVAL;
+  }
+  out->n = h->n;
+  out->ld = h->ld;
+  out->precision = (int32_t)h->prec;
+  out->num_sms = h->num_sms;
+  out->store_bytes = h->store_bytes;
+  out->setup_ms = h->setup_ms;
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_profile_begin(pide_handle h) {
+  if (!h) {
+    set_error("pide_profile_begin: bad argument");
+    return PIDE_EINVAL;
+  }
+  h->prof_on = true;
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_profile_end(pide_handle h, pide_profile* out) {
+  if (!h || !out) {
+    set_error("pide_profile_end: bad argument");
+    return PIDE_EINVAL;
+  }
+  h->prof_on = false;
+  std::memset(out, 0, sizeof(*out));
+  pide_status s = PIDE_OK;
+  for (auto& ev : h->prof_events) {
+    if (cudaEventSynchronize(ev.b) != cudaSuccess) s = PIDE_ECUDA;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) {
+      out->ms[ev.cls] += ms;
+      out->launches[ev.cls] += 1;
+    }
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  h->prof_events.clear();
+  return s;
+}
+
+extern "C" const char* pide_status_string(pide_status s) {
+  switch (s) {
+    case PIDE_OK: return "ok";
+    case PIDE_EINVAL: return "invalid argument";
+    case PIDE_ENOMEM: return "out of memory";
+    case PIDE_ECUDA: return "CUDA error";
+    case PIDE_ENOTCONV: return "refinement did not reach the tolerance";
+    case PIDE_ETIMEOUT: return "device-side wait timed out";
+    case PIDE_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* pide_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int32_t pide_version(void) { return 1; }

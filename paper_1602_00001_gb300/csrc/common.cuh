@@ -1,0 +1,328 @@
+// Internal declarations shared by the CUDA translation units of libpide.
+// Nothing here is part of the public ABI (include/pide.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pide.h"
+
+namespace pide {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+
+#define PIDE_CUDA_TRY(expr)                                                   \
+  do {                                                                        \
+    cudaError_t e__ = (expr);                                                 \
+    if (e__ != cudaSuccess) {                                                 \
+      ::pide::set_error(std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+      return e__ == cudaErrorMemoryAllocation ? PIDE_ENOMEM : PIDE_ECUDA;     \
+    }                                                                         \
+  } while (0)
+
+#define PIDE_TRY(expr)                 \
+  do {                                 \
+    pide_status s__ = (expr);          \
+    if (s__ != PIDE_OK) return s__;    \
+  } while (0)
+
+// Device-side error word values (ctx->flags[1]).
+enum : uint32_t { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_MMA = 2, DEV_TIMEOUT_EPI = 3,
+                  DEV_TIMEOUT_DRAIN = 4 };
+
+// Flag words in device memory.
+enum { FLAG_DONE = 0, FLAG_ERROR = 1, FLAG_SWEEPS = 2, FLAG_WHERE = 3, FLAG_COUNT = 8 };
+
+// ---------------------------------------------------------------- context
+
+enum ApplyKind { KIND_F64 = 0, KIND_F32 = 1, KIND_BF16 = 2, KIND_FP8 = 3, KIND_FP8X2 = 4 };
+
+struct pide_ctx_impl;
+
+}  // namespace pide
+
+struct pide_ctx {
+  // grid and operator
+  int nx = 0, ny = 0, mx = 0, my = 0, n = 0;
+  double h = 0.0;
+  pide_precision prec = PIDE_FP64;
+  int device = 0, num_sms = 0;
+  int ld = 0;                       // row stride of the stored inverse (elements)
+  double* eps = nullptr;            // [ny][nx] node permittivity
+  double* cf = nullptr;             // [4][n] face eps of each interior node: W, E, S, N
+  double* d = nullptr;              // [n] diagonal of S (sum of face eps)
+  std::vector<double> eps_host;     // kept for save/load
+  // stored inverse (S^-1, symmetric)
+  void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / e4m3 (hi)
+  void* inv_lo = nullptr;           // [n][ld] e4m3 lo term (FP8X2)
+  float* row_scale = nullptr;       // [n] per-row scale (FP8 formats)
+  size_t store_bytes = 0;
+  bool tmA_ok = false;
+  CUtensorMap tmA, tmA_lo;          // TMA maps over the stored inverse (tensor-core formats)
+  // workspace (grown on demand; pide_reserve pre-sizes it)
+  int ws_B = 0;
+  void* R = nullptr;                // [ws_B][ld] quantised right-hand side / residual
+  float* col_scale = nullptr;       // [ws_B] per-column scale (FP8 formats)
+  double* lift = nullptr;           // [n] boundary lifting, D-scaled (sum_q c_pq g_q)
+  double* colmax = nullptr;         // [3][ws_B] column maxima: |r|, |b|, raw (FP8 scales)
+  uint32_t* flags = nullptr;        // FLAG_COUNT words
+  double* hbuf_b = nullptr;         // device staging for pide_apply_host
+  double* hbuf_u = nullptr;
+  int hbuf_B = 0;
+  void* tmR_ptr = nullptr;          // which R buffer tmR describes
+  int tmR_rows = 0;
+  CUtensorMap tmR;
+  // autotuned launch choices
+  int gemm_bn_large = 256;          // BN for B >= 256
+  int gemv_max_b = 8;               // largest B sent to the GEMV kernel
+  // profiling
+  bool prof_on = false;
+  struct Ev { cudaEvent_t a, b; int cls; };
+  std::vector<Ev> prof_events;
+  double setup_ms = 0.0;
+};
+
+namespace pide {
+
+// ---------------------------------------------------------------- launchers
+// (each returns a pide_status; kernels are enqueued on `st`)
+
+pide_status launch_assemble(pide_ctx* c, cudaStream_t st);
+pide_status launch_rhs_from_charge(pide_ctx* c, const double* rho, double* b, int B, cudaStream_t st);
+pide_status launch_lift(pide_ctx* c, const double* g, cudaStream_t st);
+pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st);
+pide_status quantize_store(pide_ctx* c, const double* G, cudaStream_t st);
+
+// RHS preparation: R = q(f~), f~ = d*b + lift (mode 0) or f~ = b (mode 1).
+pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
+                        int rfmt, cudaStream_t st);
+// Residual: R = q(f~ - S u); optional column max of |r| (b-form) into colmax.
+pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
+                            const double* lift, int rfmt, bool write_R, double* r_out, bool track,
+                            bool honor_done, cudaStream_t st);
+pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
+// FP8 right-hand sides: per-column scale max|f~|/448 (prep) or max|r~|/448 (residual).
+pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int B, int mode,
+                              const double* lift, bool from_residual, cudaStream_t st);
+pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const double* lift,
+                            cudaStream_t st);
+
+// Apply: u (=|+=) Q(S^-1) R for B columns.
+pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+int rhs_format(const pide_ctx* c, int B);   // element format R must hold for this B
+
+// tensor-core GEMM (BF16, FP8X2) and SIMT paths
+pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+pide_status launch_gemm_simt(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+
+pide_status launch_face_grad(pide_ctx* c, const double* mu, const double* u, const double* b,
+                             int B, double* deps, cudaStream_t st);
+pide_status launch_scale_d(pide_ctx* c, const double* mu, double* db, int B, cudaStream_t st);
+
+pide_status ensure_workspace(pide_ctx* c, int B);
+pide_status make_tma_maps(pide_ctx* c);
+pide_status make_tma_rhs(pide_ctx* c, int bn);
+
+// event profiling around one launch of class `cls`
+struct ProfScope {
+  pide_ctx* c; cudaStream_t st; int cls; cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(pide_ctx* c_, cudaStream_t st_, int cls_);
+  ~ProfScope();
+};
+
+enum RhsFmt { RF_F64 = 0, RF_F32 = 1, RF_BF16 = 2, RF_E4M3 = 3 };
+
+size_t rhs_elem_bytes(int rfmt);
+
+// ---------------------------------------------------------------- device helpers
+
+#ifdef __CUDACC__
+
+// Budget for every spin-wait on an mbarrier, in SM clock cycles (~1 s).
+#define PIDE_WAIT_BUDGET_CYCLES (2000000000ll)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and leaves the barrier alone) once the cycle
+// budget is spent or *abort becomes non-zero.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > PIDE_WAIT_BUDGET_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 2-D tiled TMA load global -> shared, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Same with an L2 cache-policy hint.
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                                 int x, int y, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---- tcgen05 (5th-generation tensor cores, accumulators in TMEM)
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16/F16 inputs, F32 accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// kind::f8f6f4 (here: e4m3 x e4m3, F32 accumulate)
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive once on `bar` when every previously issued tcgen05.mma of this thread completes.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: thread t gets row (lane base + t).
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile stored with the
+// 128-byte swizzle (rows of 128 bytes, 8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+  desc |= (uint64_t)(16 >> 4) << 16;                 // leading byte offset (unused for SW128 K-major)
+  desc |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8-row group
+  desc |= (uint64_t)1 << 46;                         // descriptor version (tcgen05)
+  desc |= (uint64_t)2 << 61;                         // swizzle: 128B
+  return desc;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace pide

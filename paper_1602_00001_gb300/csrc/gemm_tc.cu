@@ -1,0 +1,311 @@
+// Step 3 on the 5th-generation tensor cores: U (=|+=) Q(S^-1) * R for many
+// right-hand sides, the dense contraction at the heart of the direct method.
+//
+//   A = stored inverse, [n][ld] row-major (K = q contiguous)  -> K-major operand
+//   B = right-hand sides R, [B][ld] row-major (K contiguous)   -> K-major operand
+//   D[p][col] accumulates in TMEM (FP32); the epilogue writes the FP64 result
+//   u[col][p] (one right-hand side per row of u), adding to it during sweeps.
+//
+// Persistent, warp-specialised kernel, one CTA per SM (192 threads):
+//   warp 0  TMA producer: 128 x BK tiles of A and BN x BK tiles of R per stage,
+//           128-byte swizzle, STAGES-deep ring of shared-memory buffers
+//   warp 1  allocates TMEM, one thread issues tcgen05.mma (M=128, N=BN) and
+//           commits each stage back to the producer and each finished tile to
+//           the epilogue
+//   warps 2-5  epilogue: tcgen05.ld 32 lanes x 32 columns at a time, scale,
+//           FP64 read-modify-write of u (coalesced along p)
+// The accumulator is double-buffered in TMEM (2 x BN columns) so the epilogue
+// of tile t overlaps the main loop of tile t+1.  Tiles are ordered with the
+// right-hand-side tile fastest, so the CTAs that share one 128-row slab of the
+// inverse run at the same time and the slab is read from HBM about once.
+//
+// FP8X2: A is the e4m3 hi term and A_lo the lo term (per-row scale in the
+// epilogue); both multiply the same e4m3 R tile and accumulate into the same
+// TMEM tile, i.e. one contraction with K doubled.
+//
+// Every wait on an mbarrier is bounded (about a second): on expiry the kernel
+// records an error word, lets the other roles leave, waits (bounded) for its
+// outstanding copies and MMAs, frees TMEM and returns.
+#include "common.cuh"
+
+namespace pide {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int ROW_BYTES = 128;    // K extent of one stage: one 128-byte swizzle row
+
+template <int BN, bool FP8>
+struct TcCfg {
+  static constexpr int A_BYTES = BM * ROW_BYTES;           // 16 KB
+  static constexpr int B_BYTES = BN * ROW_BYTES;
+  static constexpr int K_ELEMS = FP8 ? 128 : 64;            // elements per stage along K
+  static constexpr int K_PER_MMA_BYTES = 32;                // 16 bf16 or 32 e4m3
+  static constexpr int MMAS_PER_STAGE = ROW_BYTES / K_PER_MMA_BYTES;
+  static constexpr uint32_t TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
+};
+
+template <int BN, int STAGES, int MODE>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo)
+__global__ void __launch_bounds__(192, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+               const __grid_constant__ CUtensorMap tmR, int n, int B, int num_kb,
+               double* __restrict__ u, int accumulate, const float* __restrict__ row_scale,
+               const float* __restrict__ col_scale, uint32_t* __restrict__ flags) {
+  constexpr bool FP8 = MODE != 0;
+  constexpr bool LO = MODE == 2;
+  using C = TcCfg<BN, FP8>;
+  constexpr int A_STAGE = LO ? 2 * C::A_BYTES : C::A_BYTES;
+  constexpr uint32_t STAGE_TX = A_STAGE + C::B_BYTES;
+
+  if (flags[FLAG_DONE]) return;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * C::B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m_tiles = (n + BM - 1) / BM;
+  const int n_tiles = (B + BN - 1) / BN;
+  const int num_tiles = m_tiles * n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_s = 0;
+    fence_barrier_init();
+    prefetch_tmap(&tmA);
+    if (LO) prefetch_tmap(&tmAlo);
+    prefetch_tmap(&tmR);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    const uint64_t pol_a = policy_evict_first();   // the inverse streams through L2 once
+    const uint64_t pol_r = policy_evict_last();    // the right-hand sides are re-read by every slab
+    int s = 0;
+    uint32_t ph = 0;
+    uint32_t issued = 0;                            // bit s: stage s has a copy in flight
+    uint32_t issued_ph = 0;                         // parity of that copy's phase
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort_s)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE_TX);
+        const int kx = kb * C::K_ELEMS;
+        tma_load_2d_hint(sA + s * A_STAGE, &tmA, &full[s], kx, mt * BM, pol_a);
+        if (LO) tma_load_2d_hint(sA + s * A_STAGE + C::A_BYTES, &tmAlo, &full[s], kx, mt * BM, pol_a);
+        tma_load_2d_hint(sB + s * C::B_BYTES, &tmR, &full[s], kx, nt * BN, pol_r);
+        issued |= 1u << s;
+        issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    if (!ok) {
+      atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_TMA);
+      *abort_s = 1;
+      // wait (bounded, ignoring the abort flag) for our own copies still in flight
+      volatile int never = 0;
+      for (int t = 0; t < STAGES; ++t)
+        if (issued & (1u << t)) mbar_wait_bounded(&full[t], (issued_ph >> t) & 1u, &never);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    uint32_t idesc = (1u << 4)                                  // D: F32
+                     | ((FP8 ? 0u : 1u) << 7)                   // A: BF16 (kind::f16) / E4M3 (kind::f8f6f4)
+                     | ((FP8 ? 0u : 1u) << 10)                  // B: same
+                     | ((uint32_t)(BN >> 3) << 17)              // N
+                     | ((uint32_t)(BM >> 4) << 24);             // M
+    int s = 0;
+    uint32_t ph = 0;
+    int acc = 0;
+    uint32_t acc_ph = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      if (!mbar_wait_bounded(&tempty[acc], acc_ph ^ 1, abort_s)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait_bounded(&full[s], ph, abort_s)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(sA + s * A_STAGE);
+        const uint32_t b_addr = smem_u32(sB + s * C::B_BYTES);
+#pragma unroll
+        for (int k = 0; k < C::MMAS_PER_STAGE; ++k) {
+          const uint64_t bdesc = smem_desc_sw128(b_addr + k * C::K_PER_MMA_BYTES);
+          const uint64_t adesc = smem_desc_sw128(a_addr + k * C::K_PER_MMA_BYTES);
+          const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+          if (FP8) mma_f8(d_tmem, adesc, bdesc, idesc, accum);
+          else mma_f16(d_tmem, adesc, bdesc, idesc, accum);
+          if (LO) {
+            const uint64_t ldesc = smem_desc_sw128(a_addr + C::A_BYTES + k * C::K_PER_MMA_BYTES);
+            mma_f8(d_tmem, ldesc, bdesc, idesc, 1u);
+          }
+        }
+        mma_commit(&empty[s]);                     // frees the stage when these MMAs finish
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit(&tfull[acc]);                     // tile done -> epilogue
+      acc ^= 1;
+      if (acc == 0) acc_ph ^= 1;
+    }
+    if (!ok) {
+      atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_MMA);
+      *abort_s = 1;
+    }
+    // drain: every MMA issued above has finished once this commit arrives
+    mma_commit(drain);
+    volatile int never = 0;
+    if (!mbar_wait_bounded(drain, 0, &never)) atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_DRAIN);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;                  // TMEM lanes 32*quarter .. +31
+    const int row_in_tile = quarter * 32 + lane;
+    int acc = 0;
+    uint32_t acc_ph = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+      const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
+      bool ok = mbar_wait_bounded(&tfull[acc], acc_ph, abort_s);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_EPI);
+          *abort_s = 1;
+        }
+        break;
+      }
+      tc_fence_after();
+      const int p = mt * BM + row_in_tile;
+      const bool prow = p < n;
+      const double rs = (row_scale && prow) ? (double)row_scale[p] : 1.0;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tbase + ch * 32, v);
+        tmem_ld_wait();
+        const int colbase = nt * BN + ch * 32;
+        if (prow) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = colbase + j;
+            if (col < B) {
+              double val = (double)__uint_as_float(v[j]) * rs;
+              if (col_scale) val *= (double)col_scale[col];
+              double* dst = u + (size_t)col * n + p;
+              *dst = accumulate ? *dst + val : val;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_ph ^= 1;
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C::TMEM_COLS);
+  }
+}
+
+template <int BN, int STAGES, int MODE>
+pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+  using C = TcCfg<BN, MODE != 0>;
+  constexpr int A_STAGE = (MODE == 2) ? 2 * C::A_BYTES : C::A_BYTES;
+  const size_t smem = 1024 + (size_t)STAGES * (A_STAGE + C::B_BYTES) + 256;
+  PIDE_TRY(make_tma_rhs(c, BN));
+  auto kern = gemm_tc_kernel<BN, STAGES, MODE>;
+  PIDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int m_tiles = (c->n + BM - 1) / BM;
+  const int n_tiles = (B + BN - 1) / BN;
+  const int tiles = m_tiles * n_tiles;
+  const int grid = tiles < c->num_sms ? tiles : c->num_sms;
+  const int num_kb = (c->n + C::K_ELEMS - 1) / C::K_ELEMS;
+  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, num_kb, u,
+                                accumulate ? 1 : 0, c->row_scale,
+                                MODE != 0 ? c->col_scale : nullptr, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+template <int MODE>
+pide_status launch_tc_mode(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+  // BN: the smallest supported tile that covers B (up to 256); stages fill ~200 KB.
+  if (MODE == 0) {
+    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st);
+    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st);
+    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st);
+  } else if (MODE == 1) {
+    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st);
+    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st);
+    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st);
+  } else {
+    if (B <= 32) return launch_tc<32, 6, MODE>(c, B, u, accumulate, st);
+    if (B <= 64) return launch_tc<64, 5, MODE>(c, B, u, accumulate, st);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 4, MODE>(c, B, u, accumulate, st);
+    return launch_tc<256, 3, MODE>(c, B, u, accumulate, st);
+  }
+}
+
+}  // namespace
+
+pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+  if (!c->tmA_ok) {
+    set_error("tensor-core apply: TMA maps were not created");
+    return PIDE_EUNSUPPORTED;
+  }
+  switch (c->prec) {
+    case PIDE_BF16: return launch_tc_mode<0>(c, B, u, accumulate, st);
+    case PIDE_FP8: return launch_tc_mode<1>(c, B, u, accumulate, st);
+    case PIDE_FP8X2: return launch_tc_mode<2>(c, B, u, accumulate, st);
+    default: return PIDE_EUNSUPPORTED;
+  }
+}
+
+}  // namespace pide

@@ -1,0 +1,235 @@
+// Step 2 ("using any standard matrix inversion method"): the dense inverse of
+// the symmetric conservative operator S = D L, formed in FP64 on the GPU.
+//
+// S is block tridiagonal over grid rows: m = ny-2 diagonal blocks A_a (k x k,
+// k = nx-2, tridiagonal: d on the diagonal, -eps of the x faces beside it) and
+// diagonal couplings S_{a,a+1} = -diag(eps of the y faces between rows a, a+1).
+// Block elimination from both ends gives the whole inverse G = S^-1:
+//   backward Schur complements  Sg_{m-1} = A_{m-1},
+//                               Sg_a = A_a - C_a Sg_{a+1}^-1 C_a      (C_a = diag(north faces of row a))
+//   forward Schur complements   Df_0 = A_0,
+//                               Df_a = A_a - C_{a-1} Df_{a-1}^-1 C_{a-1}
+//   diagonal blocks             G_aa = (A_a - C_{a-1} Df_{a-1}^-1 C_{a-1} - C_a Sg_{a+1}^-1 C_a)^-1
+//   blocks below the diagonal   G_{a,j} = M_a G_{a-1,j},  M_a = Sg_a^-1 C_{a-1}   (a > j)
+//   blocks above                G_{j,a} = G_{a,j}^T        (S symmetric)
+// The two chains are sequences of k x k inversions (one CTA each, run side by
+// side); the diagonal blocks are m independent inversions; the rest is a
+// wavefront of batched k x k x k FP64 GEMMs, O(n^2 k) flops in total instead
+// of O(n^3) for dense LU.
+#include "common.cuh"
+
+namespace pide {
+
+namespace {
+
+// In-place Gauss-Jordan inversion of a k x k SPD matrix (no pivoting needed:
+// every pivot of an SPD matrix is positive).  All threads of the block take part.
+__device__ void gj_invert(double* A, int k, size_t lda, double* s_row, double* s_col,
+                          double* s_rp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int piv = 0; piv < k; ++piv) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      s_row[t] = A[(size_t)piv * lda + t];
+      s_col[t] = A[(size_t)t * lda + piv];
+    }
+    __syncthreads();
+    const double pinv = 1.0 / s_row[piv];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) s_rp[t] = s_row[t] * pinv;
+    __syncthreads();
+    for (int i = warp; i < k; i += nw) {
+      const double ci = s_col[i];
+      double* row = A + (size_t)i * lda;
+      if (i == piv) {
+        for (int j = lane; j < k; j += 32) row[j] = (j == piv) ? pinv : s_rp[j];
+      } else {
+        for (int j = lane; j < k; j += 32) row[j] = (j == piv) ? -ci * pinv : fma(-ci, s_rp[j], row[j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double block_A(const double* cf, const double* d, int n, int k, int a,
+                                          int r, int c) {
+  const int p = a * k + r;
+  if (r == c) return d[p];
+  if (c == r + 1) return -cf[n + p];        // east face of (a, r)
+  if (c == r - 1) return -cf[p];            // west face of (a, r)
+  return 0.0;
+}
+
+// blockIdx.x == 0: backward chain into Gb[a] = Sg_a^-1; == 1: forward chain into Gf[a] = Df_a^-1.
+__global__ void __launch_bounds__(1024) chain_kernel(const double* __restrict__ cf,
+                                                     const double* __restrict__ d, int k, int m,
+                                                     double* __restrict__ Gb,
+                                                     double* __restrict__ Gf) {
+  extern __shared__ double sh[];
+  double* s_row = sh;
+  double* s_col = sh + k;
+  double* s_rp = sh + 2 * k;
+  const int n = k * m;
+  const bool backward = (blockIdx.x == 0);
+  const size_t kk = (size_t)k * k;
+  for (int step = 0; step < m; ++step) {
+    const int a = backward ? (m - 1 - step) : step;
+    double* T = (backward ? Gb : Gf) + (size_t)a * kk;
+    const bool has_prev = backward ? (a < m - 1) : (a > 0);
+    const double* P = has_prev ? ((backward ? Gb : Gf) + (size_t)(backward ? a + 1 : a - 1) * kk) : nullptr;
+    // coupling faces: backward uses the north faces of row a, forward the south faces of row a
+    const double* C = backward ? (cf + 3 * (size_t)n + (size_t)a * k) : (cf + 2 * (size_t)n + (size_t)a * k);
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int r = e / k, c = e - r * k;
+      double v = block_A(cf, d, n, k, a, r, c);
+      if (has_prev) v -= C[r] * P[e] * C[c];
+      T[e] = v;
+    }
+    __syncthreads();
+    gj_invert(T, k, k, s_row, s_col, s_rp);
+  }
+}
+
+// Diagonal blocks of the inverse, one CTA per block row a, written in place
+// into G at block (a, a).
+__global__ void __launch_bounds__(1024) diag_kernel(const double* __restrict__ cf,
+                                                    const double* __restrict__ d, int k, int m,
+                                                    const double* __restrict__ Gb,
+                                                    const double* __restrict__ Gf,
+                                                    double* __restrict__ G, size_t ld) {
+  extern __shared__ double sh[];
+  const int a = blockIdx.x;
+  const int n = k * m;
+  const size_t kk = (size_t)k * k;
+  double* T = G + (size_t)a * k * ld + (size_t)a * k;
+  const double* Cs = cf + 2 * (size_t)n + (size_t)a * k;
+  const double* Cn = cf + 3 * (size_t)n + (size_t)a * k;
+  const double* Pf = (a > 0) ? Gf + (size_t)(a - 1) * kk : nullptr;
+  const double* Pb = (a < m - 1) ? Gb + (size_t)(a + 1) * kk : nullptr;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int r = e / k, c = e - r * k;
+    double v = block_A(cf, d, n, k, a, r, c);
+    if (Pf) v -= Cs[r] * Pf[e] * Cs[c];
+    if (Pb) v -= Cn[r] * Pb[e] * Cn[c];
+    T[(size_t)r * ld + c] = v;
+  }
+  __syncthreads();
+  gj_invert(T, k, ld, sh, sh + k, sh + 2 * k);
+}
+
+// M_a = Sg_a^-1 diag(south faces of row a) for a >= 1, in place over Gb[a].
+__global__ void mscale_kernel(const double* __restrict__ cf, int k, int m, double* __restrict__ Gb) {
+  const int n = k * m;
+  const size_t kk = (size_t)k * k;
+  const size_t total = (size_t)(m - 1) * kk;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int a = 1 + (int)(e / kk);
+    const int c = (int)((e % kk) % k);
+    Gb[kk + e] *= cf[2 * (size_t)n + (size_t)a * k + c];
+  }
+}
+
+// One wavefront step s: for every j with a = j + s < m, G(a, j) = M_a G(a-1, j).
+// 64 x 64 output tile per CTA, 256 threads with 4 x 4 results each, K in steps of 16.
+__global__ void __launch_bounds__(256) wave_dgemm(const double* __restrict__ Mw,
+                                                  double* __restrict__ G, size_t ld, int k,
+                                                  int s) {
+  __shared__ double As[16][65];
+  __shared__ double Xs[16][65];
+  const int j = blockIdx.z, a = j + s;
+  const double* A = Mw + (size_t)a * k * k;
+  const double* X = G + (size_t)(a - 1) * k * ld + (size_t)j * k;
+  double* C = G + (size_t)a * k * ld + (size_t)j * k;
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
+  for (int k0 = 0; k0 < k; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      const int r = e >> 4, kk = e & 15;
+      const int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < k && gk < k) ? A[(size_t)gr * k + gk] : 0.0;
+      const int kk2 = e >> 6, cc = e & 63;
+      const int gk2 = k0 + kk2, gc = col0 + cc;
+      Xs[kk2][cc] = (gk2 < k && gc < k) ? X[(size_t)gk2 * ld + gc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], xv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = Xs[kk][tx + 16 * q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = fma(av[i], xv[q], acc[i][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= k) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = col0 + tx + 16 * q;
+      if (c < k) C[(size_t)r * ld + c] = acc[i][q];
+    }
+  }
+}
+
+// Upper blocks from the lower ones: G[p][q] = G[q][p] when block(p) < block(q).
+__global__ void mirror_kernel(double* __restrict__ G, size_t ld, int n, int k) {
+  __shared__ double t[32][33];
+  const int tr = blockIdx.y * 32, tc = blockIdx.x * 32;   // destination tile (rows tr.., cols tc..)
+  if ((tr + 31) / k >= tc / k && tr / k >= (tc + 31) / k) return;  // no element strictly above
+  // load the source tile: rows tc.., cols tr.. (transposed position)
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int sr = tc + r, sc = tr + threadIdx.x;
+    t[r][threadIdx.x] = (sr < n && sc < n) ? G[(size_t)sr * ld + sc] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int dr = tr + r, dc = tc + threadIdx.x;
+    if (dr < n && dc < n && dr / k < dc / k) G[(size_t)dr * ld + dc] = t[threadIdx.x][r];
+  }
+}
+
+}  // namespace
+
+pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st) {
+  const int k = c->mx, m = c->my;
+  const size_t kk = (size_t)k * k;
+  double* work = nullptr;
+  PIDE_CUDA_TRY(cudaMallocAsync((void**)&work, 2 * (size_t)m * kk * sizeof(double), st));
+  double* Gb = work;
+  double* Gf = work + (size_t)m * kk;
+  const size_t shm = 3 * (size_t)k * sizeof(double);
+  chain_kernel<<<2, 1024, shm, st>>>(c->cf, c->d, k, m, Gb, Gf);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  diag_kernel<<<m, 1024, shm, st>>>(c->cf, c->d, k, m, Gb, Gf, G, (size_t)c->ld);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  if (m > 1) {
+    mscale_kernel<<<c->num_sms * 4, 256, 0, st>>>(c->cf, k, m, Gb);
+    PIDE_CUDA_TRY(cudaGetLastError());
+    const int tiles = (k + 63) / 64;
+    for (int s = 1; s < m; ++s) {
+      dim3 grid(tiles, tiles, m - s);
+      wave_dgemm<<<grid, 256, 0, st>>>(Gb, G, (size_t)c->ld, k, s);
+      PIDE_CUDA_TRY(cudaGetLastError());
+    }
+    dim3 mg((c->n + 31) / 32, (c->n + 31) / 32);
+    mirror_kernel<<<mg, dim3(32, 8), 0, st>>>(G, (size_t)c->ld, c->n, k);
+    PIDE_CUDA_TRY(cudaGetLastError());
+  }
+  PIDE_CUDA_TRY(cudaFreeAsync(work, st));
+  return PIDE_OK;
+}
+
+}  // namespace pide

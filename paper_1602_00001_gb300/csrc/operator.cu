@@ -1,0 +1,403 @@
+// Operator kernels: assembly of the 5-point system (Eq. 2/3), right-hand
+// side preparation, the FP64 stencil residual, and the adjoint face gradient.
+//
+// Layout: interior node p = a*mx + c (a = i-1, c = j-1, j fastest, the order of
+// Fig. 3 restricted to the interior).  cf holds four face permittivities per
+// node, structure of arrays: cf[0*n+p] west (j-1), cf[1*n+p] east (j+1),
+// cf[2*n+p] south (i-1), cf[3*n+p] north (i+1).  d[p] = their sum, so that
+// S = D - (off-diagonal face terms) and L = D^-1 S is the row of Eq. (3).
+#include "common.cuh"
+
+namespace pide {
+
+namespace {
+
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+// Step 1 (assembly): face eps by harmonic mean of the two node values, d = sum.
+__global__ void assemble_kernel(const double* __restrict__ eps, int nx, int ny,
+                                double* __restrict__ cf, double* __restrict__ d) {
+  const int mx = nx - 2, my = ny - 2, n = mx * my;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int a = p / mx, c = p - a * mx;
+    const int i = a + 1, j = c + 1;
+    const double e0 = eps[i * nx + j];
+    const double w = harmonic(e0, eps[i * nx + j - 1]);
+    const double e = harmonic(e0, eps[i * nx + j + 1]);
+    const double s = harmonic(e0, eps[(i - 1) * nx + j]);
+    const double no = harmonic(e0, eps[(i + 1) * nx + j]);
+    cf[p] = w;
+    cf[n + p] = e;
+    cf[2 * n + p] = s;
+    cf[3 * n + p] = no;
+    d[p] = w + e + s + no;
+  }
+}
+
+// b = -h^2 rho / d  (flux form of Eq. 1 divided by the node's total face eps)
+__global__ void rhs_from_charge_kernel(const double* __restrict__ rho, double* __restrict__ b,
+                                       const double* __restrict__ d, int n, long long total,
+                                       double h2) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(k % n);
+    b[k] = -h2 * rho[k] / d[p];
+  }
+}
+
+// lift_p = sum over boundary neighbours q of eps_pq g_q  (Fig. 3's boundary
+// columns moved to the right side, in the D-scaled form S u = D b + lift)
+__global__ void lift_kernel(const double* __restrict__ g, const double* __restrict__ cf, int nx,
+                            int ny, double* __restrict__ lift) {
+  const int mx = nx - 2, my = ny - 2, n = mx * my;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int a = p / mx, c = p - a * mx;
+    const int i = a + 1, j = c + 1;
+    double s = 0.0;
+    if (c == 0) s += cf[p] * g[i * nx + j - 1];
+    if (c == mx - 1) s += cf[n + p] * g[i * nx + j + 1];
+    if (a == 0) s += cf[2 * n + p] * g[(i - 1) * nx + j];
+    if (a == my - 1) s += cf[3 * n + p] * g[(i + 1) * nx + j];
+    lift[p] = s;
+  }
+}
+
+template <int RF>
+__device__ __forceinline__ void store_rhs(void* R, size_t idx, double v, float inv_scale) {
+  if constexpr (RF == RF_F64) {
+    reinterpret_cast<double*>(R)[idx] = v;
+  } else if constexpr (RF == RF_F32) {
+    reinterpret_cast<float*>(R)[idx] = (float)v;
+  } else if constexpr (RF == RF_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(R)[idx] = __double2bfloat16(v);
+  } else {
+    reinterpret_cast<__nv_fp8_e4m3*>(R)[idx] = __nv_fp8_e4m3((float)(v * (double)inv_scale));
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Prep: f~ = d*b + lift (mode 0, forward) or f~ = b (mode 1, adjoint: S mu = g).
+// R[col][p] = q(f~); colmax_b[col] = max_p |f~_p / d_p| (b-form magnitude).
+template <int RF>
+__global__ void prep_kernel(const double* __restrict__ b, int n, int ldr, int mode,
+                            const double* __restrict__ d, const double* __restrict__ lift,
+                            void* __restrict__ R, const float* __restrict__ col_scale,
+                            double* __restrict__ colmax_b, int track) {
+  __shared__ double red[32];
+  const int col = blockIdx.y;
+  const double* bc = b + (size_t)col * n;
+  const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
+  double mx = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const double dp = d[p];
+    double f = bc[p];
+    if (mode == 0) f = fma(dp, f, lift ? lift[p] : 0.0);
+    store_rhs<RF>(R, (size_t)col * ldr + p, f, isc);
+    if (track) mx = fmax(mx, fabs(f) / dp);
+  }
+  if (track) {
+    mx = block_max(mx, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&colmax_b[col], mx);
+  }
+}
+
+// Residual of the S form, FP64:  r~ = f~ - S u,
+//   (S u)_p = d_p u_p - sum_q eps_pq u_q over interior neighbours q,
+// written quantised to R (the next apply's right side), optionally in b form
+// (r = r~ / d = b - L u) to r_out, and its column max |r| into colmax_r.
+template <int RF>
+__global__ void residual_kernel(const double* __restrict__ b, const double* __restrict__ u,
+                                int n, int mx, int ldr, int mode, const double* __restrict__ cf,
+                                const double* __restrict__ d, const double* __restrict__ lift,
+                                void* __restrict__ R, const float* __restrict__ col_scale,
+                                double* __restrict__ r_out, double* __restrict__ colmax_r,
+                                int track, int track_raw, const uint32_t* __restrict__ flags) {
+  __shared__ double red[32];
+  if (flags && flags[FLAG_DONE]) return;
+  const int col = blockIdx.y;
+  const double* uc = u + (size_t)col * n;
+  const double* bc = b + (size_t)col * n;
+  const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
+  double mxr = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int c = p % mx;
+    const double dp = d[p];
+    double f = bc[p];
+    if (mode == 0) f = fma(dp, f, lift ? lift[p] : 0.0);
+    double r = fma(-dp, uc[p], f);
+    if (c > 0) r = fma(cf[p], uc[p - 1], r);
+    if (c < mx - 1) r = fma(cf[n + p], uc[p + 1], r);
+    if (p >= mx) r = fma(cf[2 * n + p], uc[p - mx], r);
+    if (p + mx < n) r = fma(cf[3 * n + p], uc[p + mx], r);
+    if (R) store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
+    if (r_out) r_out[(size_t)col * n + p] = r / dp;
+    if (track) mxr = fmax(mxr, track_raw ? fabs(r) : fabs(r) / dp);
+  }
+  if (track) {
+    mxr = block_max(mxr, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&colmax_r[col], mxr);
+  }
+}
+
+// Convergence check between sweeps: done once every column satisfies
+// max|r| <= tol * max|f/d|.  Resets the residual maxima for the next sweep.
+__global__ void check_kernel(double* colmax, const double* colmax_b, int B, double tol,
+                             uint32_t* flags) {
+  __shared__ int bad;
+  if (flags[FLAG_DONE]) return;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < B; c += blockDim.x) {
+    if (colmax[c] > tol * colmax_b[c]) bad = 1;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < B; c += blockDim.x) colmax[c] = 0.0;
+  if (threadIdx.x == 0) {
+    if (!bad) flags[FLAG_DONE] = 1;
+    else flags[FLAG_SWEEPS] += 1;
+  }
+}
+
+// Column maxima of |f~/d| without writing R (for pide_apply's tol / info).
+__global__ void colmax_b_kernel(const double* __restrict__ b, int n, int mode,
+                                const double* __restrict__ d, const double* __restrict__ lift,
+                                double* __restrict__ colmax_b) {
+  __shared__ double red[32];
+  const int col = blockIdx.y;
+  const double* bc = b + (size_t)col * n;
+  double mx = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    double f = bc[p];
+    if (mode == 0) f = fma(d[p], f, lift ? lift[p] : 0.0);
+    mx = fmax(mx, fabs(f) / d[p]);
+  }
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(&colmax_b[col], mx);
+}
+
+// Adjoint, per node a of the grid: dLoss/deps_a = sum over the node's faces f
+// (to node b) of T_f * 2 eps_b^2 / (eps_a + eps_b)^2, where
+//   T_f = sum_cols mu_p b_p + mu_q b_q - (mu_p - mu_q)(u_p - u_q)
+// and a boundary endpoint contributes mu = 0, no b term and u = 0.  Each node
+// gathers its own faces (no atomics; each face total is formed twice).
+__global__ void face_grad_kernel(const double* __restrict__ mu, const double* __restrict__ u,
+                                 const double* __restrict__ b, const double* __restrict__ eps,
+                                 int nx, int ny, int B, double* __restrict__ deps) {
+  const int mx = nx - 2, n = mx * (ny - 2);
+  const int N = nx * ny;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N;
+       node += gridDim.x * blockDim.x) {
+    const int i = node / nx, j = node - i * nx;
+    const bool in_a = (i > 0 && i < ny - 1 && j > 0 && j < nx - 1);
+    const int pa = in_a ? (i - 1) * mx + (j - 1) : -1;
+    const double ea = eps[node];
+    double acc = 0.0;
+    const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
+    for (int k = 0; k < 4; ++k) {
+      const int i2 = i + di[k], j2 = j + dj[k];
+      if (i2 < 0 || i2 >= ny || j2 < 0 || j2 >= nx) continue;
+      const bool in_b = (i2 > 0 && i2 < ny - 1 && j2 > 0 && j2 < nx - 1);
+      if (!in_a && !in_b) continue;
+      const int pb = in_b ? (i2 - 1) * mx + (j2 - 1) : -1;
+      double T = 0.0;
+      for (int c = 0; c < B; ++c) {
+        const size_t o = (size_t)c * n;
+        const double mua = in_a ? mu[o + pa] : 0.0, mub = in_b ? mu[o + pb] : 0.0;
+        const double ua = in_a ? u[o + pa] : 0.0, ub = in_b ? u[o + pb] : 0.0;
+        const double ba = in_a ? b[o + pa] : 0.0, bb = in_b ? b[o + pb] : 0.0;
+        T += mua * ba + mub * bb - (mua - mub) * (ua - ub);
+      }
+      const double eb = eps[i2 * nx + j2];
+      acc += T * 2.0 * eb * eb / ((ea + eb) * (ea + eb));
+    }
+    deps[node] += acc;
+  }
+}
+
+__global__ void scale_d_kernel(const double* __restrict__ mu, const double* __restrict__ d,
+                               double* __restrict__ out, int n, long long total) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x)
+    out[k] = mu[k] * d[k % n];
+}
+
+inline int grid_for(long long work, int block, int num_sms) {
+  long long g = (work + block - 1) / block;
+  long long cap = (long long)num_sms * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+pide_status launch_assemble(pide_ctx* c, cudaStream_t st) {
+  assemble_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(c->eps, c->nx, c->ny, c->cf,
+                                                                    c->d);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_rhs_from_charge(pide_ctx* c, const double* rho, double* b, int B,
+                                   cudaStream_t st) {
+  const long long total = (long long)B * c->n;
+  if (total == 0) return PIDE_OK;
+  ProfScope ps(c, st, 2);
+  rhs_from_charge_kernel<<<grid_for(total, 256, c->num_sms), 256, 0, st>>>(rho, b, c->d, c->n,
+                                                                          total, c->h * c->h);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_lift(pide_ctx* c, const double* g, cudaStream_t st) {
+  lift_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(g, c->cf, c->nx, c->ny, c->lift);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+static dim3 col_grid(int n, int B) {
+  int gx = (n + 255) / 256;
+  if (gx > 1024) gx = 1024;
+  return dim3(gx, B, 1);
+}
+
+pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
+                        int rfmt, cudaStream_t st) {
+  if (B == 0) return PIDE_OK;
+  ProfScope ps(c, st, 2);
+  dim3 g = col_grid(c->n, B);
+  double* cmb = c->colmax + c->ws_B;
+  switch (rfmt) {
+    case RF_F64: prep_kernel<RF_F64><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, nullptr, cmb, 1); break;
+    case RF_F32: prep_kernel<RF_F32><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, nullptr, cmb, 1); break;
+    case RF_BF16: prep_kernel<RF_BF16><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, nullptr, cmb, 1); break;
+    default: prep_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, c->col_scale, cmb, 1); break;
+  }
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
+                            const double* lift, int rfmt, bool write_R, double* r_out, bool track,
+                            bool honor_done, cudaStream_t st) {
+  if (B == 0) return PIDE_OK;
+  ProfScope ps(c, st, 1);
+  dim3 g = col_grid(c->n, B);
+  void* R = write_R ? c->R : nullptr;
+  const uint32_t* fl = honor_done ? c->flags : nullptr;
+  double* cm = c->colmax;
+  const int t = track ? 1 : 0;
+  const int tr = 0;
+  switch (rfmt) {
+    case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, nullptr, r_out, cm, t, tr, fl); break;
+    case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, nullptr, r_out, cm, t, tr, fl); break;
+    case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, nullptr, r_out, cm, t, tr, fl); break;
+    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, c->col_scale, r_out, cm, t, tr, fl); break;
+  }
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st) {
+  ProfScope ps(c, st, 3);
+  check_kernel<<<1, 256, 0, st>>>(c->colmax, c->colmax + c->ws_B, B, tol, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const double* lift,
+                            cudaStream_t st) {
+  if (B == 0) return PIDE_OK;
+  colmax_b_kernel<<<col_grid(c->n, B), 256, 0, st>>>(b, c->n, mode, c->d, lift,
+                                                     c->colmax + c->ws_B);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_face_grad(pide_ctx* c, const double* mu, const double* u, const double* b,
+                             int B, double* deps, cudaStream_t st) {
+  ProfScope ps(c, st, 3);
+  const int N = c->nx * c->ny;
+  face_grad_kernel<<<grid_for(N, 128, c->num_sms), 128, 0, st>>>(mu, u, b, c->eps, c->nx, c->ny,
+                                                                 B, deps);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_scale_d(pide_ctx* c, const double* mu, double* db, int B, cudaStream_t st) {
+  const long long total = (long long)B * c->n;
+  if (total == 0) return PIDE_OK;
+  scale_d_kernel<<<grid_for(total, 256, c->num_sms), 256, 0, st>>>(mu, c->d, db, c->n, total);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+namespace {
+
+// FP8 right-hand sides: max |f~| per column (prep) ...
+__global__ void colmax_raw_prep_kernel(const double* __restrict__ b, int n, int mode,
+                                       const double* __restrict__ d,
+                                       const double* __restrict__ lift,
+                                       double* __restrict__ colmax_raw) {
+  __shared__ double red[32];
+  const int col = blockIdx.y;
+  const double* bc = b + (size_t)col * n;
+  double mx = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    double f = bc[p];
+    if (mode == 0) f = fma(d[p], f, lift ? lift[p] : 0.0);
+    mx = fmax(mx, fabs(f));
+  }
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(&colmax_raw[col], mx);
+}
+
+// ... and the per-column scale max/448 (448 = largest finite e4m3); resets the maxima.
+__global__ void finalize_scale_kernel(double* __restrict__ colmax_raw, float* __restrict__ col_scale,
+                                      int B, const uint32_t* __restrict__ flags) {
+  if (flags && flags[FLAG_DONE]) return;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < B; c += gridDim.x * blockDim.x) {
+    const double m = colmax_raw[c];
+    col_scale[c] = m > 0.0 ? (float)(m / 448.0) : 1.0f;
+    colmax_raw[c] = 0.0;
+  }
+}
+
+}  // namespace
+
+pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int B, int mode,
+                              const double* lift, bool from_residual, cudaStream_t st) {
+  if (B == 0) return PIDE_OK;
+  ProfScope ps(c, st, 2);
+  dim3 g = col_grid(c->n, B);
+  double* raw = c->colmax + 2 * (size_t)c->ws_B;
+  if (from_residual) {
+    residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift,
+                                               nullptr, nullptr, nullptr, raw, 1, 1, c->flags);
+  } else {
+    colmax_raw_prep_kernel<<<g, 256, 0, st>>>(b, c->n, mode, c->d, lift, raw);
+  }
+  PIDE_CUDA_TRY(cudaGetLastError());
+  finalize_scale_kernel<<<(B + 255) / 256, 256, 0, st>>>(raw, c->col_scale, B, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+}  // namespace pide

@@ -1,0 +1,70 @@
+"""The C ABI: the library builds, loads and exports every entry point that
+include/pide.h declares (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import pide_oracle as O
+from paper_1602_00001_gb300 import binding
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1602_00001_gb300 import build
+    build.build()
+    return binding.load_library()
+
+
+def test_header_declares_the_boundary():
+    syms = binding.header_symbols()
+    for name in ["pide_setup", "pide_apply", "pide_residual", "pide_apply_backward",
+                 "pide_apply_batched", "pide_destroy"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = binding.LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [s for s in binding.header_symbols() if s not in exported]
+    assert not missing, missing
+    for s in binding.header_symbols():
+        assert hasattr(lib, s)
+
+
+def test_status_strings_and_version(lib):
+    assert lib.pide_version() == 1
+    assert lib.pide_status_string(0) == b"ok"
+    assert b"invalid" in lib.pide_status_string(1)
+
+
+def test_setup_rejects_bad_grid_without_gpu(lib):
+    """Argument checks happen on the host before any CUDA call."""
+    h = ctypes.c_void_p()
+    g = binding.Grid(2, 5, 0.1)
+    assert lib.pide_setup(ctypes.byref(g), None, 2, None, ctypes.byref(h)) == 1
+    g = binding.Grid(5, 5, -1.0)
+    assert lib.pide_setup(ctypes.byref(g), None, 2, None, ctypes.byref(h)) == 1
+    g = binding.Grid(5, 5, 0.25)
+    assert lib.pide_setup(ctypes.byref(g), None, 9, None, ctypes.byref(h)) == 1
+    assert not h.value
+    assert lib.pide_apply(None, None, None, 1, 0, 0.0, None, None, None) == 1
+
+
+def test_oracle_binary_rounding_pins():
+    """round_bf16 / round_fp32 against torch's conversions on float32-exact
+    inputs (where a conversion through float32 rounds once), plus ties."""
+    import torch
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(4000).astype(np.float32).astype(np.float64) * 10.0 ** rng.integers(-8, 8, 4000)
+    x = x.astype(np.float32).astype(np.float64)
+    ref = torch.from_numpy(x).to(torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_bf16(x), ref)
+    y = rng.standard_normal(1000) * 1e3
+    assert np.array_equal(O.round_fp32(y), y.astype(np.float32).astype(np.float64))
+    # ties to even: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> 1
+    assert O.round_bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert O.round_bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the plain FP64 path within 1e-12 (Eq. 6 relative error, worst
+column); the refined low-precision paths within 1e-6; single low-precision
+applies against the oracle's contraction of the same rounded operands within
+a bound derived from FP32 accumulation.
+"""
+import numpy as np
+import pytest
+
+from oracle import pide_oracle as O
+from paper_1602_00001_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1602_00001_gb300 import build, binding
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build.build()
+    binding.load_library()
+
+
+def _solver(nx, ny, h, eps, prec):
+    from paper_1602_00001_gb300.binding import Solver
+    return Solver(nx, ny, h, eps, prec)
+
+
+def _b(nx, ny, h, eps, B, seed):
+    rho = W.gaussian_blobs(nx, ny, h, seed, batch=B)
+    return O.rhs_from_charge(nx, ny, h, eps, rho)
+
+
+GRIDS = [(3, 3), (3, 7), (7, 3), (5, 5), (12, 9), (21, 21), (34, 27)]
+
+
+@pytest.mark.parametrize("nx,ny", GRIDS)
+@pytest.mark.parametrize("B", [1, 2, 5, 9, 70])
+def test_fp64_apply_matches_oracle(nx, ny, B):
+    h = 1.0 / (max(nx, ny) - 1)
+    eps = W.eps_lognormal(nx, ny, seed=nx * 31 + ny)
+    b = W.random_interior(nx, ny, seed=B, batch=B)
+    s = _solver(nx, ny, h, eps, "fp64")
+    u = s.apply(b).cpu().numpy()
+    ref = O.solve(nx, ny, eps, b)
+    assert O.rel_error_eq6(u, ref) < 1e-12
+
+
+def test_fp64_inverse_rows_match_oracle():
+    nx, ny = 14, 11
+    eps = W.eps_fourier(nx, ny, 1.0 / 13, seed=2)
+    s = _solver(nx, ny, 1.0 / 13, eps, "fp64")
+    Linv = O.interior_inverse(nx, ny, eps)
+    d = O.diagonal_d(nx, ny, eps)
+    Sinv = Linv / d[None, :]          # S^-1 = L^-1 D^-1
+    for p in [0, 5, s.n // 2, s.n - 1]:
+        row = s.inverse_row(p)
+        assert np.max(np.abs(row - Sinv[p])) < 1e-13 * np.max(np.abs(Sinv))
+
+
+def test_fig3_grid_eps1():
+    """nx=3, ny=5 at eps=1 (Fig. 3): three unknowns."""
+    s = _solver(3, 5, 0.25, None, "fp64")
+    b = np.array([[1.0, 2.0, 3.0]])
+    u = s.apply(b).cpu().numpy()
+    A = O.assemble_full(3, 5)
+    uf = O.lu_inverse(A) @ O.full_rhs(3, 5, b)[0]
+    assert np.max(np.abs(u[0] - uf[[4, 7, 10]])) < 1e-15
+
+
+def test_residual_matches_oracle():
+    nx, ny = 23, 17
+    h = 1.0 / 22
+    eps = W.eps_lognormal(nx, ny, seed=5)
+    s = _solver(nx, ny, h, eps, "fp64")
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal((3, s.n))
+    u = rng.standard_normal((3, s.n))
+    r = s.residual(b, u).cpu().numpy()
+    ref = O.residual(nx, ny, eps, b, u)
+    assert np.max(np.abs(r - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+def test_rhs_from_charge_matches_oracle():
+    nx, ny = 19, 15
+    h = 1.0 / 18
+    eps = W.eps_fourier(nx, ny, h, seed=3)
+    s = _solver(nx, ny, h, eps, "fp64")
+    rho = W.gaussian_blobs(nx, ny, h, seed=4, batch=2)
+    b = s.rhs_from_charge(rho).cpu().numpy()
+    assert np.max(np.abs(b - O.rhs_from_charge(nx, ny, h, eps, rho))) <= 1e-15 * np.max(np.abs(b))
+
+
+def test_nonzero_boundary_values():
+    """Fig. 3's boundary rows carry boundary values: lifting on the GPU."""
+    nx, ny = 16, 12
+    h = 1.0 / 15
+    eps = W.eps_lognormal(nx, ny, seed=6)
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal((ny, nx))
+    b = rng.standard_normal((2, (nx - 2) * (ny - 2)))
+    s = _solver(nx, ny, h, eps, "fp64")
+    u = s.apply(b, g=torch.from_numpy(g)).cpu().numpy()
+    ref = O.solve(nx, ny, eps, b, g)
+    assert O.rel_error_eq6(u, ref) < 1e-12
+
+
+# ----------------------------------------------------------- low-precision contraction
+
+
+def _oracle_lowprec_apply(nx, ny, eps, b, store_round, rhs_round):
+    """Q(S^-1) q(D b) in FP64 with the operands rounded like the GPU stores them."""
+    Linv = O.interior_inverse(nx, ny, eps)
+    d = O.diagonal_d(nx, ny, eps)
+    Q = store_round(Linv / d[None, :])
+    f = rhs_round(b * d[None, :])
+    return (Q @ f.T).T, (np.abs(Q) @ np.abs(f).T).T
+
+
+@pytest.mark.parametrize("B", [1, 3, 8, 9, 40, 64, 65, 130, 300])
+def test_bf16_single_apply_is_exact_contraction(B):
+    """One apply (no refinement) equals the FP64 contraction of the same
+    bf16-rounded inverse and right-hand side up to FP32 accumulation; B <= 8
+    takes the GEMV (FP32 right-hand side), larger B the tcgen05 GEMM."""
+    nx, ny = 40, 33
+    h = 1.0 / 39
+    eps = W.eps_fourier(nx, ny, h, seed=11)
+    b = _b(nx, ny, h, eps, B, seed=B)
+    s = _solver(nx, ny, h, eps, "bf16")
+    u = s.apply(b, sweeps=0).cpu().numpy()
+    rhs_round = O.round_fp32 if B <= 8 else O.round_bf16
+    ref, mag = _oracle_lowprec_apply(nx, ny, eps, b, O.round_bf16, rhs_round)
+    err = np.abs(u - ref)
+    assert np.all(err <= 2e-5 * mag + 1e-300), float(np.max(err / mag))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("B", [1, 9, 64, 257])
+def test_refined_reaches_1e6(prec, B):
+    nx = ny = 50
+    h = 1.0 / 49
+    eps = W.eps_fourier(nx, ny, h, seed=1)
+    b = _b(nx, ny, h, eps, B, seed=100 + B)
+    s = _solver(nx, ny, h, eps, prec)
+    u, info = s.apply(b, sweeps=10, tol=1e-10, want_info=True)
+    ref = O.solve(nx, ny, eps, b, route="band")
+    assert O.rel_error_eq6(u.cpu().numpy(), ref) < 1e-6
+    assert info.converged == 1 and info.rel_residual <= 1e-10
+
+
+def test_refinement_contracts():
+    """Each sweep shrinks the error (the stored inverse is a contraction
+    preconditioner for this grid)."""
+    nx = ny = 50
+    h = 1.0 / 49
+    eps = W.eps_fourier(nx, ny, h, seed=1)
+    b = _b(nx, ny, h, eps, 32, seed=5)
+    ref = O.solve(nx, ny, eps, b, route="band")
+    s = _solver(nx, ny, h, eps, "bf16")
+    errs = [O.rel_error_eq6(s.apply(b, sweeps=k).cpu().numpy(), ref) for k in range(4)]
+    assert errs[0] < 2e-2
+    for a, c in zip(errs, errs[1:]):
+        assert c < 0.5 * a, errs
+
+
+def test_edge_cases():
+    s = _solver(9, 8, 0.125, None, "bf16")
+    empty = torch.empty((0, s.n), dtype=torch.float64, device="cuda")
+    assert s.apply(empty).shape == (0, s.n)
+    from paper_1602_00001_gb300.binding import PideError
+    with pytest.raises(PideError):
+        _solver(6, 6, 0.2, -np.ones((6, 6)), "bf16")
+    b = torch.zeros((2, s.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(PideError):
+        s.apply(b, u=b)
+    # zero right-hand side -> zero solution, in every path
+    for B in (1, 20):
+        z = torch.zeros((B, s.n), dtype=torch.float64, device="cuda")
+        assert float(s.apply(z, sweeps=2).abs().max()) == 0.0
+
+
+def test_apply_host_matches_device():
+    nx = ny = 30
+    h = 1.0 / 29
+    eps = W.eps_lognormal(nx, ny, seed=9)
+    b = _b(nx, ny, h, eps, 12, seed=3)
+    s = _solver(nx, ny, h, eps, "bf16")
+    ud = s.apply(b, sweeps=3).cpu().numpy()
+    uh = s.apply_host(b, sweeps=3)
+    assert np.array_equal(ud, uh)
+
+
+def test_save_load_roundtrip(tmp_path):
+    nx, ny = 26, 21
+    h = 1.0 / 25
+    eps = W.eps_lognormal(nx, ny, seed=12)
+    from paper_1602_00001_gb300.binding import Solver
+    s = Solver(nx, ny, h, eps, "bf16")
+    b = _b(nx, ny, h, eps, 20, seed=1)
+    u1 = s.apply(b, sweeps=2).cpu().numpy()
+    path = str(tmp_path / "inv.pide")
+    s.save(path)
+    s2 = Solver.load(path)
+    u2 = s2.apply(b, sweeps=2).cpu().numpy()
+    assert np.array_equal(u1, u2)
