@@ -155,6 +155,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--nodes", type=int, default=NODES, help="grid nodes per side (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -177,14 +178,15 @@ def main():
     from paper_1602_00001_gb300.binding import Solver
 
     B = args.batch
-    h = 1.0 / (NODES - 1)
-    eps = W.eps_fourier(NODES, NODES, h, seed=5)
-    rho_np = W.moving_charges(NODES, NODES, h, seed=5 + rank, steps=B)
+    NN = args.nodes
+    h = 1.0 / (NN - 1)
+    eps = W.eps_fourier(NN, NN, h, seed=5)
+    rho_np = W.moving_charges(NN, NN, h, seed=5 + rank, steps=B)
     stream = torch.cuda.current_stream()
 
     # ---- the plain FP64 GPU apply: reference solution for sampled columns and
     #      the comparator rate (FP64 is compute bound at any B on this part)
-    s64 = Solver(NODES, NODES, h, eps, "fp64")
+    s64 = Solver(NN, NN, h, eps, "fp64")
     rho = torch.from_numpy(rho_np).cuda()
     b = s64.rhs_from_charge(rho)
     sample_cols = list(range(0, B, max(B // 16, 1)))[:16]
@@ -211,7 +213,7 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- the refined low-precision solver
-    s = Solver(NODES, NODES, h, eps, args.precision)
+    s = Solver(NN, NN, h, eps, args.precision)
     s.reserve(B)
     n = s.n
     u = torch.empty((B, n), dtype=torch.float64, device="cuda")
@@ -302,8 +304,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": B * world, "per_gpu_batch": B,
-                   "grid": f"{NODES}x{NODES}", "unknowns": n, "precision": args.precision,
+        "config": {"workload": WORKLOAD if NN == NODES else f"{NN - 2}^2 interior, B={B}",
+                   "global_batch": B * world, "per_gpu_batch": B,
+                   "grid": f"{NN}x{NN}", "unknowns": n, "precision": args.precision,
                    "sweeps": k, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (3.07 GB BF16 inverse streamed per apply)"},
         "accuracy": {"max_rel_err_eq6_vs_fp64": err_final, "target": 1e-6,
@@ -328,7 +331,7 @@ def main():
         from oracle import pide_oracle as O
         cols = 4
         b_np = b[:cols].cpu().numpy()
-        rate, dt, fac, u_or = cpu_oracle_rate(NODES, NODES, h, eps, b_np, cols)
+        rate, dt, fac, u_or = cpu_oracle_rate(NN, NN, h, eps, b_np, cols)
         ur = u[:cols].cpu().numpy()
         line["accuracy"]["max_rel_err_eq6_vs_oracle_2col"] = O.rel_error_eq6(ur[:2], u_or[:2])
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",

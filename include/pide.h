@@ -203,9 +203,24 @@ pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out);
 pide_status pide_profile_begin(pide_handle h);
 pide_status pide_profile_end(pide_handle h, pide_profile* out);
 
-/* Copy the stored inverse's row p (converted to float64, scales applied) to
- * host memory dst[n]: lets tests check individual entries. */
+/* Copy row p of the stored inverse L^-1 (converted to float64, scales
+ * applied) to host memory dst[n]: lets tests check individual entries. */
 pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
+
+/* Launch-shape knobs of the apply kernels (set by the autotuner; results do
+ * not depend on them beyond FP32 summation order).
+ *   PIDE_TUNE_GEMV_THREADS  GEMV block size: 128..1024, multiple of 32 (default 1024)
+ *   PIDE_TUNE_GEMV_UNROLL   16-byte loads in flight per lane: 4 or 8 (default 8)
+ *   PIDE_TUNE_GEMV_MAX_B    largest B served by the GEMV instead of the GEMM: 1..8 (default 1)
+ *   PIDE_TUNE_GEMM_BN       tensor-core tile width for B > 128: 128 or 256 (default 256) */
+typedef enum {
+  PIDE_TUNE_GEMV_THREADS = 0,
+  PIDE_TUNE_GEMV_UNROLL = 1,
+  PIDE_TUNE_GEMV_MAX_B = 2,
+  PIDE_TUNE_GEMM_BN = 3
+} pide_tune_key;
+pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
+pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);
 
 const char* pide_status_string(pide_status s);
 const char* pide_last_error(void);

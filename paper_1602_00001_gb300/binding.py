@@ -66,6 +66,8 @@ _SIGS = {
     "pide_profile_begin": (_I, [_P]),
     "pide_profile_end": (_I, [_P, ctypes.POINTER(Profile)]),
     "pide_get_inverse_row": (_I, [_P, _I, _P]),
+    "pide_set_tuning": (_I, [_P, _I, _I]),
+    "pide_get_tuning": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "pide_status_string": (ctypes.c_char_p, [_I]),
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),
@@ -229,6 +231,21 @@ class Solver:
                                             _ptr(deps), gout.shape[0], int(sweeps),
                                             _stream(stream)), "pide_apply_backward")
         return db, deps
+
+    TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3}
+
+    def set_tuning(self, **kv):
+        for k, v in kv.items():
+            _check(self.lib.pide_set_tuning(self.handle, self.TUNE_KEYS[k], int(v)),
+                   "pide_set_tuning")
+
+    def get_tuning(self) -> dict:
+        out = {}
+        for k, key in self.TUNE_KEYS.items():
+            v = ctypes.c_int32()
+            _check(self.lib.pide_get_tuning(self.handle, key, ctypes.byref(v)), "pide_get_tuning")
+            out[k] = v.value
+        return out
 
     def reserve(self, Bmax: int):
         _check(self.lib.pide_reserve(self.handle, int(Bmax)), "pide_reserve")

@@ -148,8 +148,9 @@ pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStr
   return launch_gemm_tc(c, B, u, accumulate, st);
 }
 
-// S x = rhs~ with x = Q(S^-1) q(rhs~), then `sweeps` refinement sweeps
-// x += Q(S^-1) q(rhs~ - S x).  mode 0: rhs~ = D b + lift; mode 1: rhs~ = b.
+// L x = f with x = Q(L^-1) q(f), then `sweeps` refinement sweeps
+// x += Q(L^-1) q(f - L x), the residual in FP64.  mode 0: f = b + lift (Eq. 3);
+// mode 1 (adjoint): f = b / d, so that x = L^-1 D^-1 b = S^-1 b.
 static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, double* x,
                            int B, int sweeps, double tol, cudaStream_t st) {
   PIDE_TRY(ensure_workspace(c, B));
@@ -157,7 +158,7 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
   PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, 3 * (size_t)c->ws_B * sizeof(double), st));
   const int rf = rhs_format(c, B);
   if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
-  PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, st));
+  PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
   for (int k = 0; k < sweeps; ++k) {
     if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, x, B, mode, lift, true, st));
@@ -173,6 +174,10 @@ static pide_status fill_info(pide_ctx* c, const double* b, const double* x, int 
                              pide_info* info) {
   // one more residual, tracked, ignoring the early-exit flag
   PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, (size_t)c->ws_B * sizeof(double), st));
+  if (tol <= 0) {
+    PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax + c->ws_B, 0, (size_t)c->ws_B * sizeof(double), st));
+    PIDE_TRY(launch_colmax_b(c, b, B, mode, lift, st));
+  }
   PIDE_TRY(launch_residual(c, b, x, B, mode, lift, RF_F64, false, nullptr, true, false, st));
   std::vector<double> cm(2 * (size_t)c->ws_B);
   uint32_t fl[FLAG_COUNT];
@@ -260,6 +265,8 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->eps, N * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->cf, 4 * (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->d, (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->dinv, (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->w, 4 * (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->lift, (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->flags, FLAG_COUNT * sizeof(uint32_t)));
   PIDE_CUDA_TRY(cudaMemset(c->flags, 0, FLAG_COUNT * sizeof(uint32_t)));
@@ -326,7 +333,7 @@ extern "C" void pide_destroy(pide_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {h->eps, h->cf, h->d, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
+  void* ptrs[] = {h->eps, h->cf, h->d, h->dinv, h->w, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
                   h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -652,6 +659,48 @@ extern "C" pide_status pide_profile_end(pide_handle h, pide_profile* out) {
   }
   h->prof_events.clear();
   return s;
+}
+
+extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value) {
+  if (!h) {
+    set_error("pide_set_tuning: NULL handle");
+    return PIDE_EINVAL;
+  }
+  switch (key) {
+    case PIDE_TUNE_GEMV_THREADS:
+      if (value < 128 || value > 1024 || value % 32) break;
+      h->gemv_threads = value;
+      return PIDE_OK;
+    case PIDE_TUNE_GEMV_UNROLL:
+      if (value != 4 && value != 8) break;
+      h->gemv_unroll = value;
+      return PIDE_OK;
+    case PIDE_TUNE_GEMV_MAX_B:
+      if (value < 1 || value > 8) break;
+      h->gemv_max_b = value;
+      return PIDE_OK;
+    case PIDE_TUNE_GEMM_BN:
+      if (value != 128 && value != 256) break;
+      h->gemm_bn_large = value;
+      return PIDE_OK;
+  }
+  set_error("pide_set_tuning: unknown key or value out of range");
+  return PIDE_EINVAL;
+}
+
+extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value) {
+  if (!h || !value) {
+    set_error("pide_get_tuning: bad argument");
+    return PIDE_EINVAL;
+  }
+  switch (key) {
+    case PIDE_TUNE_GEMV_THREADS: *value = h->gemv_threads; return PIDE_OK;
+    case PIDE_TUNE_GEMV_UNROLL: *value = h->gemv_unroll; return PIDE_OK;
+    case PIDE_TUNE_GEMV_MAX_B: *value = h->gemv_max_b; return PIDE_OK;
+    case PIDE_TUNE_GEMM_BN: *value = h->gemm_bn_large; return PIDE_OK;
+  }
+  set_error("pide_get_tuning: unknown key");
+  return PIDE_EINVAL;
 }
 
 extern "C" const char* pide_status_string(pide_status s) {

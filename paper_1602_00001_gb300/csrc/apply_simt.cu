@@ -47,11 +47,8 @@ __device__ __forceinline__ void unpack(const uint4& raw, float (&out)[Elem<KIND>
   }
 }
 
-constexpr int GEMV_THREADS = 512;
-constexpr int GEMV_UNROLL = 4;
-
-template <int KIND, int NB>
-__global__ void __launch_bounds__(GEMV_THREADS) gemv_kernel(
+template <int KIND, int NB, int GEMV_UNROLL>
+__global__ void __launch_bounds__(1024) gemv_kernel(
     const void* __restrict__ A_, const void* __restrict__ Alo_, const float* __restrict__ row_scale,
     const float* __restrict__ col_scale, int n, int ld, const void* __restrict__ R_, int ldr,
     int B, double* __restrict__ u, int accumulate, int kchunk, const uint32_t* __restrict__ flags) {
@@ -203,12 +200,12 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const TA* __restrict__ A
   }
 }
 
-template <int KIND, int NB>
+template <int KIND, int NB, int UNROLL>
 pide_status gemv_launch(pide_ctx* c, int B, int col0, double* u, bool accumulate,
                         cudaStream_t st) {
   using TX = typename Elem<KIND>::TX;
   constexpr int VEC = Elem<KIND>::VEC;
-  const int unit = 32 * VEC * GEMV_UNROLL;
+  const int unit = 32 * VEC * UNROLL;
   const size_t smem_cap = 200 * 1024;
   int kchunk = (int)(smem_cap / (NB * sizeof(TX)));
   kchunk = (kchunk / unit) * unit;
@@ -216,7 +213,7 @@ pide_status gemv_launch(pide_ctx* c, int B, int col0, double* u, bool accumulate
   if (kchunk > npad) kchunk = npad;
   const int ksplit = (c->n + kchunk - 1) / kchunk;
   const size_t smem = (size_t)NB * kchunk * sizeof(TX);
-  auto kern = gemv_kernel<KIND, NB>;
+  auto kern = gemv_kernel<KIND, NB, UNROLL>;
   PIDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int bcols = B - col0 < NB ? B - col0 : NB;
   double* uc = u + (size_t)col0 * c->n;
@@ -225,10 +222,18 @@ pide_status gemv_launch(pide_ctx* c, int B, int col0, double* u, bool accumulate
   const size_t esz = rhs_elem_bytes(rhs_format(c, B));
   const void* R = (const uint8_t*)c->R + (size_t)col0 * c->ld * esz;
   dim3 grid(c->num_sms, ksplit);
-  kern<<<grid, GEMV_THREADS, smem, st>>>(c->inv, c->inv_lo, c->row_scale, nullptr, c->n, c->ld,
-                                         R, c->ld, bcols, uc, accumulate ? 1 : 0, kchunk, c->flags);
+  kern<<<grid, c->gemv_threads, smem, st>>>(c->inv, c->inv_lo, c->row_scale, nullptr, c->n, c->ld,
+                                            R, c->ld, bcols, uc, accumulate ? 1 : 0, kchunk,
+                                            c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
+}
+
+template <int KIND, int NB>
+pide_status gemv_unroll(pide_ctx* c, int B, int col0, double* u, bool accumulate, cudaStream_t st) {
+  // FP8X2 keeps two vectors per load slot: cap its unroll to stay within 64 registers
+  if (c->gemv_unroll >= 8 && KIND != KIND_FP8X2) return gemv_launch<KIND, NB, 8>(c, B, col0, u, accumulate, st);
+  return gemv_launch<KIND, NB, 4>(c, B, col0, u, accumulate, st);
 }
 
 template <int KIND>
@@ -236,10 +241,10 @@ pide_status gemv_dispatch(pide_ctx* c, int B, double* u, bool accumulate, cudaSt
   for (int col0 = 0; col0 < B; col0 += 8) {
     const int left = B - col0;
     pide_status s;
-    if (left == 1) s = gemv_launch<KIND, 1>(c, B, col0, u, accumulate, st);
-    else if (left == 2) s = gemv_launch<KIND, 2>(c, B, col0, u, accumulate, st);
-    else if (left <= 4) s = gemv_launch<KIND, 4>(c, B, col0, u, accumulate, st);
-    else s = gemv_launch<KIND, 8>(c, B, col0, u, accumulate, st);
+    if (left == 1) s = gemv_unroll<KIND, 1>(c, B, col0, u, accumulate, st);
+    else if (left == 2) s = gemv_unroll<KIND, 2>(c, B, col0, u, accumulate, st);
+    else if (left <= 4) s = gemv_unroll<KIND, 4>(c, B, col0, u, accumulate, st);
+    else s = gemv_unroll<KIND, 8>(c, B, col0, u, accumulate, st);
     if (s != PIDE_OK) return s;
   }
   return PIDE_OK;

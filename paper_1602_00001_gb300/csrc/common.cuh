@@ -59,8 +59,10 @@ struct pide_ctx {
   double* eps = nullptr;            // [ny][nx] node permittivity
   double* cf = nullptr;             // [4][n] face eps of each interior node: W, E, S, N
   double* d = nullptr;              // [n] diagonal of S (sum of face eps)
+  double* dinv = nullptr;           // [n] 1 / d
+  double* w = nullptr;              // [4][n] Eq. (3) weights w = cf / d
   std::vector<double> eps_host;     // kept for save/load
-  // stored inverse (S^-1, symmetric)
+  // stored inverse L^-1 = S^-1 D (the interior block of the Fig. 3 inverse)
   void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / e4m3 (hi)
   void* inv_lo = nullptr;           // [n][ld] e4m3 lo term (FP8X2)
   float* row_scale = nullptr;       // [n] per-row scale (FP8 formats)
@@ -71,7 +73,7 @@ struct pide_ctx {
   int ws_B = 0;
   void* R = nullptr;                // [ws_B][ld] quantised right-hand side / residual
   float* col_scale = nullptr;       // [ws_B] per-column scale (FP8 formats)
-  double* lift = nullptr;           // [n] boundary lifting, D-scaled (sum_q c_pq g_q)
+  double* lift = nullptr;           // [n] boundary lifting sum_q w_pq g_q
   double* colmax = nullptr;         // [3][ws_B] column maxima: |r|, |b|, raw (FP8 scales)
   uint32_t* flags = nullptr;        // FLAG_COUNT words
   double* hbuf_b = nullptr;         // device staging for pide_apply_host
@@ -80,9 +82,11 @@ struct pide_ctx {
   void* tmR_ptr = nullptr;          // which R buffer tmR describes
   int tmR_rows = 0;
   CUtensorMap tmR;
-  // autotuned launch choices
-  int gemm_bn_large = 256;          // BN for B >= 256
-  int gemv_max_b = 8;               // largest B sent to the GEMV kernel
+  // launch-shape knobs (pide_set_tuning; the autotuner sets them)
+  int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
+  int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
+  int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
+  int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8
   // profiling
   bool prof_on = false;
   struct Ev { cudaEvent_t a, b; int cls; };
@@ -98,13 +102,13 @@ namespace pide {
 pide_status launch_assemble(pide_ctx* c, cudaStream_t st);
 pide_status launch_rhs_from_charge(pide_ctx* c, const double* rho, double* b, int B, cudaStream_t st);
 pide_status launch_lift(pide_ctx* c, const double* g, cudaStream_t st);
-pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st);
+pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st);   // G = L^-1 (FP64)
 pide_status quantize_store(pide_ctx* c, const double* G, cudaStream_t st);
 
-// RHS preparation: R = q(f~), f~ = d*b + lift (mode 0) or f~ = b (mode 1).
+// RHS preparation: R = q(f), f = b + lift (mode 0) or f = b / d (mode 1, adjoint).
 pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
-                        int rfmt, cudaStream_t st);
-// Residual: R = q(f~ - S u); optional column max of |r| (b-form) into colmax.
+                        int rfmt, bool track, cudaStream_t st);
+// Residual: R = q(f - L u) (FP64 stencil); optional column max of |r| into colmax.
 pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
                             bool honor_done, cudaStream_t st);
@@ -115,7 +119,7 @@ pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int
 pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const double* lift,
                             cudaStream_t st);
 
-// Apply: u (=|+=) Q(S^-1) R for B columns.
+// Apply: u (=|+=) Q(L^-1) R for B columns.
 pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 int rhs_format(const pide_ctx* c, int B);   // element format R must hold for this B
 

@@ -15,7 +15,7 @@
 // The two chains are sequences of k x k inversions (one CTA each, run side by
 // side); the diagonal blocks are m independent inversions; the rest is a
 // wavefront of batched k x k x k FP64 GEMMs, O(n^2 k) flops in total instead
-// of O(n^3) for dense LU.
+// of O(n^3) for dense LU.  Finally L^-1 = G D (Eq. 3's rows are D^-1 S).
 #include "common.cuh"
 
 namespace pide {
@@ -184,6 +184,17 @@ __global__ void __launch_bounds__(256) wave_dgemm(const double* __restrict__ Mw,
   }
 }
 
+// L^-1 = S^-1 D: scale column q by d_q (the stored inverse is that of Eq. 3's rows).
+__global__ void colscale_kernel(double* __restrict__ G, size_t ld, int n,
+                                const double* __restrict__ d) {
+  const size_t total = (size_t)n * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % ld);
+    if (q < n) G[e] *= d[q];
+  }
+}
+
 // Upper blocks from the lower ones: G[p][q] = G[q][p] when block(p) < block(q).
 __global__ void mirror_kernel(double* __restrict__ G, size_t ld, int n, int k) {
   __shared__ double t[32][33];
@@ -228,6 +239,8 @@ pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st) {
     mirror_kernel<<<mg, dim3(32, 8), 0, st>>>(G, (size_t)c->ld, c->n, k);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
+  colscale_kernel<<<c->num_sms * 8, 256, 0, st>>>(G, (size_t)c->ld, c->n, c->d);
+  PIDE_CUDA_TRY(cudaGetLastError());
   PIDE_CUDA_TRY(cudaFreeAsync(work, st));
   return PIDE_OK;
 }

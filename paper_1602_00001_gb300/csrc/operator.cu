@@ -5,7 +5,10 @@
 // Fig. 3 restricted to the interior).  cf holds four face permittivities per
 // node, structure of arrays: cf[0*n+p] west (j-1), cf[1*n+p] east (j+1),
 // cf[2*n+p] south (i-1), cf[3*n+p] north (i+1).  d[p] = their sum, so that
-// S = D - (off-diagonal face terms) and L = D^-1 S is the row of Eq. (3).
+// S = D - (off-diagonal face terms) is symmetric and L = D^-1 S is the row of
+// Eq. (3): u_p - sum_q w_pq u_q with w = cf / d (stored in w, same layout).
+// The stored inverse is L^-1 itself, so every right-hand side is in the
+// Eq. (3) form and the residual is r = b - u + sum_q w_pq u_q.
 #include "common.cuh"
 
 namespace pide {
@@ -16,7 +19,8 @@ __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a 
 
 // Step 1 (assembly): face eps by harmonic mean of the two node values, d = sum.
 __global__ void assemble_kernel(const double* __restrict__ eps, int nx, int ny,
-                                double* __restrict__ cf, double* __restrict__ d) {
+                                double* __restrict__ cf, double* __restrict__ d,
+                                double* __restrict__ w4, double* __restrict__ dinv) {
   const int mx = nx - 2, my = ny - 2, n = mx * my;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int a = p / mx, c = p - a * mx;
@@ -30,7 +34,13 @@ __global__ void assemble_kernel(const double* __restrict__ eps, int nx, int ny,
     cf[n + p] = e;
     cf[2 * n + p] = s;
     cf[3 * n + p] = no;
-    d[p] = w + e + s + no;
+    const double dp = w + e + s + no;
+    d[p] = dp;
+    dinv[p] = 1.0 / dp;
+    w4[p] = w / dp;
+    w4[n + p] = e / dp;
+    w4[2 * n + p] = s / dp;
+    w4[3 * n + p] = no / dp;
   }
 }
 
@@ -41,12 +51,12 @@ __global__ void rhs_from_charge_kernel(const double* __restrict__ rho, double* _
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
     const int p = (int)(k % n);
-    b[k] = -h2 * rho[k] / d[p];
+    b[k] = -h2 * rho[k] / d[p];   // one division per entry; not on the refined path
   }
 }
 
-// lift_p = sum over boundary neighbours q of eps_pq g_q  (Fig. 3's boundary
-// columns moved to the right side, in the D-scaled form S u = D b + lift)
+// lift_p = sum over boundary neighbours q of w_pq g_q  (Fig. 3's boundary
+// columns moved to the right side of Eq. 3)
 __global__ void lift_kernel(const double* __restrict__ g, const double* __restrict__ cf, int nx,
                             int ny, double* __restrict__ lift) {
   const int mx = nx - 2, my = ny - 2, n = mx * my;
@@ -93,11 +103,13 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return v;
 }
 
-// Prep: f~ = d*b + lift (mode 0, forward) or f~ = b (mode 1, adjoint: S mu = g).
-// R[col][p] = q(f~); colmax_b[col] = max_p |f~_p / d_p| (b-form magnitude).
+// Prep: the right-hand side the stored L^-1 is applied to,
+//   mode 0 (forward):  f = b + lift           (Eq. 3 right side)
+//   mode 1 (adjoint):  f = g / d              (S mu = g  <=>  L mu = D^-1 g)
+// R[col][p] = q(f); optionally colmax_b[col] = max_p |f_p|.
 template <int RF>
 __global__ void prep_kernel(const double* __restrict__ b, int n, int ldr, int mode,
-                            const double* __restrict__ d, const double* __restrict__ lift,
+                            const double* __restrict__ dinv, const double* __restrict__ lift,
                             void* __restrict__ R, const float* __restrict__ col_scale,
                             double* __restrict__ colmax_b, int track) {
   __shared__ double red[32];
@@ -106,11 +118,11 @@ __global__ void prep_kernel(const double* __restrict__ b, int n, int ldr, int mo
   const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
   double mx = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const double dp = d[p];
     double f = bc[p];
-    if (mode == 0) f = fma(dp, f, lift ? lift[p] : 0.0);
+    if (mode == 1) f *= dinv[p];
+    else if (lift) f += lift[p];
     store_rhs<RF>(R, (size_t)col * ldr + p, f, isc);
-    if (track) mx = fmax(mx, fabs(f) / dp);
+    if (track) mx = fmax(mx, fabs(f));
   }
   if (track) {
     mx = block_max(mx, red);
@@ -118,17 +130,17 @@ __global__ void prep_kernel(const double* __restrict__ b, int n, int ldr, int mo
   }
 }
 
-// Residual of the S form, FP64:  r~ = f~ - S u,
-//   (S u)_p = d_p u_p - sum_q eps_pq u_q over interior neighbours q,
-// written quantised to R (the next apply's right side), optionally in b form
-// (r = r~ / d = b - L u) to r_out, and its column max |r| into colmax_r.
+// Residual of Eq. (3), FP64, five FP64 operations per node:
+//   r = f - L u = f - u_p + sum_q w_pq u_q   (interior neighbours q only)
+// with f as in prep.  Written quantised to R (the next apply's right side),
+// optionally in full to r_out, and its column max |r| into colmax_r.
 template <int RF>
 __global__ void residual_kernel(const double* __restrict__ b, const double* __restrict__ u,
-                                int n, int mx, int ldr, int mode, const double* __restrict__ cf,
-                                const double* __restrict__ d, const double* __restrict__ lift,
+                                int n, int mx, int ldr, int mode, const double* __restrict__ w4,
+                                const double* __restrict__ dinv, const double* __restrict__ lift,
                                 void* __restrict__ R, const float* __restrict__ col_scale,
                                 double* __restrict__ r_out, double* __restrict__ colmax_r,
-                                int track, int track_raw, const uint32_t* __restrict__ flags) {
+                                int track, const uint32_t* __restrict__ flags) {
   __shared__ double red[32];
   if (flags && flags[FLAG_DONE]) return;
   const int col = blockIdx.y;
@@ -138,17 +150,17 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
   double mxr = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int c = p % mx;
-    const double dp = d[p];
-    double f = bc[p];
-    if (mode == 0) f = fma(dp, f, lift ? lift[p] : 0.0);
-    double r = fma(-dp, uc[p], f);
-    if (c > 0) r = fma(cf[p], uc[p - 1], r);
-    if (c < mx - 1) r = fma(cf[n + p], uc[p + 1], r);
-    if (p >= mx) r = fma(cf[2 * n + p], uc[p - mx], r);
-    if (p + mx < n) r = fma(cf[3 * n + p], uc[p + mx], r);
+    double r;
+    if (mode == 1) r = fma(bc[p], dinv[p], -uc[p]);
+    else if (lift) r = bc[p] + (lift[p] - uc[p]);
+    else r = bc[p] - uc[p];
+    if (c > 0) r = fma(w4[p], uc[p - 1], r);
+    if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
+    if (p >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
+    if (p + mx < n) r = fma(w4[3 * n + p], uc[p + mx], r);
     if (R) store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
-    if (r_out) r_out[(size_t)col * n + p] = r / dp;
-    if (track) mxr = fmax(mxr, track_raw ? fabs(r) : fabs(r) / dp);
+    if (r_out) r_out[(size_t)col * n + p] = r;
+    if (track) mxr = fmax(mxr, fabs(r));
   }
   if (track) {
     mxr = block_max(mxr, red);
@@ -175,9 +187,9 @@ __global__ void check_kernel(double* colmax, const double* colmax_b, int B, doub
   }
 }
 
-// Column maxima of |f~/d| without writing R (for pide_apply's tol / info).
+// Column maxima of |f| (the prep right side) without writing R.
 __global__ void colmax_b_kernel(const double* __restrict__ b, int n, int mode,
-                                const double* __restrict__ d, const double* __restrict__ lift,
+                                const double* __restrict__ dinv, const double* __restrict__ lift,
                                 double* __restrict__ colmax_b) {
   __shared__ double red[32];
   const int col = blockIdx.y;
@@ -185,8 +197,9 @@ __global__ void colmax_b_kernel(const double* __restrict__ b, int n, int mode,
   double mx = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     double f = bc[p];
-    if (mode == 0) f = fma(d[p], f, lift ? lift[p] : 0.0);
-    mx = fmax(mx, fabs(f) / d[p]);
+    if (mode == 1) f *= dinv[p];
+    else if (lift) f += lift[p];
+    mx = fmax(mx, fabs(f));
   }
   mx = block_max(mx, red);
   if (threadIdx.x == 0) atomic_max_nonneg(&colmax_b[col], mx);
@@ -250,7 +263,7 @@ inline int grid_for(long long work, int block, int num_sms) {
 
 pide_status launch_assemble(pide_ctx* c, cudaStream_t st) {
   assemble_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(c->eps, c->nx, c->ny, c->cf,
-                                                                    c->d);
+                                                                    c->d, c->w, c->dinv);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
@@ -267,7 +280,7 @@ pide_status launch_rhs_from_charge(pide_ctx* c, const double* rho, double* b, in
 }
 
 pide_status launch_lift(pide_ctx* c, const double* g, cudaStream_t st) {
-  lift_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(g, c->cf, c->nx, c->ny, c->lift);
+  lift_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(g, c->w, c->nx, c->ny, c->lift);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
@@ -279,16 +292,17 @@ static dim3 col_grid(int n, int B) {
 }
 
 pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
-                        int rfmt, cudaStream_t st) {
+                        int rfmt, bool track, cudaStream_t st) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 2);
   dim3 g = col_grid(c->n, B);
   double* cmb = c->colmax + c->ws_B;
+  const int t = track ? 1 : 0;
   switch (rfmt) {
-    case RF_F64: prep_kernel<RF_F64><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, nullptr, cmb, 1); break;
-    case RF_F32: prep_kernel<RF_F32><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, nullptr, cmb, 1); break;
-    case RF_BF16: prep_kernel<RF_BF16><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, nullptr, cmb, 1); break;
-    default: prep_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->d, lift, c->R, c->col_scale, cmb, 1); break;
+    case RF_F64: prep_kernel<RF_F64><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->dinv, lift, c->R, nullptr, cmb, t); break;
+    case RF_F32: prep_kernel<RF_F32><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->dinv, lift, c->R, nullptr, cmb, t); break;
+    case RF_BF16: prep_kernel<RF_BF16><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->dinv, lift, c->R, nullptr, cmb, t); break;
+    default: prep_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, c->n, c->ld, mode, c->dinv, lift, c->R, c->col_scale, cmb, t); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -304,12 +318,11 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
   const uint32_t* fl = honor_done ? c->flags : nullptr;
   double* cm = c->colmax;
   const int t = track ? 1 : 0;
-  const int tr = 0;
   switch (rfmt) {
-    case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, nullptr, r_out, cm, t, tr, fl); break;
-    case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, nullptr, r_out, cm, t, tr, fl); break;
-    case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, nullptr, r_out, cm, t, tr, fl); break;
-    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift, R, c->col_scale, r_out, cm, t, tr, fl); break;
+    case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, c->col_scale, r_out, cm, t, fl); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -325,7 +338,7 @@ pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st) {
 pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const double* lift,
                             cudaStream_t st) {
   if (B == 0) return PIDE_OK;
-  colmax_b_kernel<<<col_grid(c->n, B), 256, 0, st>>>(b, c->n, mode, c->d, lift,
+  colmax_b_kernel<<<col_grid(c->n, B), 256, 0, st>>>(b, c->n, mode, c->dinv, lift,
                                                      c->colmax + c->ws_B);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -353,7 +366,7 @@ namespace {
 
 // FP8 right-hand sides: max |f~| per column (prep) ...
 __global__ void colmax_raw_prep_kernel(const double* __restrict__ b, int n, int mode,
-                                       const double* __restrict__ d,
+                                       const double* __restrict__ dinv,
                                        const double* __restrict__ lift,
                                        double* __restrict__ colmax_raw) {
   __shared__ double red[32];
@@ -362,7 +375,8 @@ __global__ void colmax_raw_prep_kernel(const double* __restrict__ b, int n, int 
   double mx = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     double f = bc[p];
-    if (mode == 0) f = fma(d[p], f, lift ? lift[p] : 0.0);
+    if (mode == 1) f *= dinv[p];
+    else if (lift) f += lift[p];
     mx = fmax(mx, fabs(f));
   }
   mx = block_max(mx, red);
@@ -389,10 +403,10 @@ pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int
   dim3 g = col_grid(c->n, B);
   double* raw = c->colmax + 2 * (size_t)c->ws_B;
   if (from_residual) {
-    residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->cf, c->d, lift,
-                                               nullptr, nullptr, nullptr, raw, 1, 1, c->flags);
+    residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift,
+                                               nullptr, nullptr, nullptr, raw, 1, c->flags);
   } else {
-    colmax_raw_prep_kernel<<<g, 256, 0, st>>>(b, c->n, mode, c->d, lift, raw);
+    colmax_raw_prep_kernel<<<g, 256, 0, st>>>(b, c->n, mode, c->dinv, lift, raw);
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   finalize_scale_kernel<<<(B + 255) / 256, 256, 0, st>>>(raw, c->col_scale, B, c->flags);
