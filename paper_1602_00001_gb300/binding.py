@@ -232,7 +232,8 @@ class Solver:
                                             _stream(stream)), "pide_apply_backward")
         return db, deps
 
-    TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3}
+    TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3,
+                 "gemm_streamk": 4}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

@@ -683,6 +683,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 128 && value != 256) break;
       h->gemm_bn_large = value;
       return PIDE_OK;
+    case PIDE_TUNE_GEMM_STREAMK:
+      if (value != 0 && value != 1) break;
+      h->gemm_streamk = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -698,6 +702,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_GEMV_UNROLL: *value = h->gemv_unroll; return PIDE_OK;
     case PIDE_TUNE_GEMV_MAX_B: *value = h->gemv_max_b; return PIDE_OK;
     case PIDE_TUNE_GEMM_BN: *value = h->gemm_bn_large; return PIDE_OK;
+    case PIDE_TUNE_GEMM_STREAMK: *value = h->gemm_streamk; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

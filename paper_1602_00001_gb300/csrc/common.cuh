@@ -84,6 +84,7 @@ struct pide_ctx {
   CUtensorMap tmR;
   // launch-shape knobs (pide_set_tuning; the autotuner sets them)
   int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
+  int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
   int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
   int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8

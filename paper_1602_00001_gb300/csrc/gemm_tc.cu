@@ -19,6 +19,15 @@
 // right-hand-side tile fastest, so the CTAs that share one 128-row slab of the
 // inverse run at the same time and the slab is read from HBM about once.
 //
+// Schedule: data-parallel waves plus a stream-K tail (Osama, Merrill, Cecka,
+// Garland, "Stream-K: Work-centric Parallel Decomposition for Dense
+// Matrix-Matrix Multiplication on the GPU", PPoPP 2023).  All but the last
+// one-and-a-bit waves of tiles go round-robin to the CTAs whole; the tiles
+// left over are cut into k-block units and every CTA takes an equal,
+// contiguous share, so no SM idles in a partial last wave.  A CTA that holds
+// only part of a tile's K range adds its partial sum into u with FP64 atomic
+// adds (those tiles are zeroed first when the apply overwrites u).
+//
 // FP8X2: A is the e4m3 hi term and A_lo the lo term (per-row scale in the
 // epilogue); both multiply the same e4m3 R tile and accumulate into the same
 // TMEM tile, i.e. one contraction with K doubled.
@@ -45,12 +54,42 @@ struct TcCfg {
   static constexpr uint32_t TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
 };
 
+// The (tile, k-block range) segments one CTA works through, identical for all roles.
+struct SegIter {
+  int G, dp_tiles, num_kb, t_dp;
+  long long u, u1;
+  __device__ SegIter(int dp, int nkb, long long sk_units)
+      : G((int)gridDim.x), dp_tiles(dp), num_kb(nkb), t_dp((int)blockIdx.x) {
+    u = sk_units * blockIdx.x / gridDim.x;
+    u1 = sk_units * (blockIdx.x + 1) / gridDim.x;
+  }
+  __device__ bool next(int& tile, int& kb0, int& kb1) {
+    if (t_dp < dp_tiles) {
+      tile = t_dp;
+      kb0 = 0;
+      kb1 = num_kb;
+      t_dp += G;
+      return true;
+    }
+    if (u < u1) {
+      tile = dp_tiles + (int)(u / num_kb);
+      kb0 = (int)(u % num_kb);
+      const long long left = u1 - u;
+      kb1 = (kb0 + left < num_kb) ? kb0 + (int)left : num_kb;
+      u += kb1 - kb0;
+      return true;
+    }
+    return false;
+  }
+};
+
 template <int BN, int STAGES, int MODE>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo)
 __global__ void __launch_bounds__(192, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
-               const __grid_constant__ CUtensorMap tmR, int n, int B, int num_kb,
-               double* __restrict__ u, int accumulate, const float* __restrict__ row_scale,
-               const float* __restrict__ col_scale, uint32_t* __restrict__ flags) {
+               const __grid_constant__ CUtensorMap tmR, int n, int B, int num_kb, int dp_tiles,
+               long long sk_units, double* __restrict__ u, int accumulate,
+               const float* __restrict__ row_scale, const float* __restrict__ col_scale,
+               uint32_t* __restrict__ flags) {
   constexpr bool FP8 = MODE != 0;
   constexpr bool LO = MODE == 2;
   using C = TcCfg<BN, FP8>;
@@ -72,9 +111,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tiles = (n + BM - 1) / BM;
   const int n_tiles = (B + BN - 1) / BN;
-  const int num_tiles = m_tiles * n_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -110,9 +147,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint32_t issued = 0;                            // bit s: stage s has a copy in flight
     uint32_t issued_ph = 0;                         // parity of that copy's phase
     bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+    SegIter it(dp_tiles, num_kb, sk_units);
+    int tile, kb0, kb1;
+    while (ok && it.next(tile, kb0, kb1)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
-      for (int kb = 0; kb < num_kb; ++kb) {
+      for (int kb = kb0; kb < kb1; ++kb) {
         if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort_s)) {
           ok = false;
           break;
@@ -150,14 +189,16 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     int acc = 0;
     uint32_t acc_ph = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+    SegIter it(dp_tiles, num_kb, sk_units);
+    int tile, kb0, kb1;
+    while (ok && it.next(tile, kb0, kb1)) {
       if (!mbar_wait_bounded(&tempty[acc], acc_ph ^ 1, abort_s)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-      for (int kb = 0; kb < num_kb; ++kb) {
+      for (int kb = kb0; kb < kb1; ++kb) {
         if (!mbar_wait_bounded(&full[s], ph, abort_s)) {
           ok = false;
           break;
@@ -169,7 +210,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int k = 0; k < C::MMAS_PER_STAGE; ++k) {
           const uint64_t bdesc = smem_desc_sw128(b_addr + k * C::K_PER_MMA_BYTES);
           const uint64_t adesc = smem_desc_sw128(a_addr + k * C::K_PER_MMA_BYTES);
-          const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+          const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
           if (FP8) mma_f8(d_tmem, adesc, bdesc, idesc, accum);
           else mma_f16(d_tmem, adesc, bdesc, idesc, accum);
           if (LO) {
@@ -202,8 +243,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int row_in_tile = quarter * 32 + lane;
     int acc = 0;
     uint32_t acc_ph = 0;
-    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+    SegIter it(dp_tiles, num_kb, sk_units);
+    int tile, kb0, kb1;
+    while (it.next(tile, kb0, kb1)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
+      const bool whole = (kb0 == 0 && kb1 == num_kb);
       bool ok = mbar_wait_bounded(&tfull[acc], acc_ph, abort_s);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
@@ -232,7 +276,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               double val = (double)__uint_as_float(v[j]) * rs;
               if (col_scale) val *= (double)col_scale[col];
               double* dst = u + (size_t)col * n + p;
-              *dst = accumulate ? *dst + val : val;
+              if (!whole) atomicAdd(dst, val);
+              else *dst = accumulate ? *dst + val : val;
             }
           }
         }
@@ -252,6 +297,18 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
+// Zero the output tiles that the stream-K tail will build from atomic partial sums.
+__global__ void zero_tiles_kernel(double* __restrict__ u, int n, int B, int bm, int bn,
+                                  int n_tiles, int first_tile, const uint32_t* __restrict__ flags) {
+  if (flags[FLAG_DONE]) return;
+  const int tile = first_tile + blockIdx.x;
+  const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
+  for (int e = threadIdx.x; e < bm * bn; e += blockDim.x) {
+    const int col = nt * bn + e / bm, p = mt * bm + e % bm;
+    if (col < B && p < n) u[(size_t)col * n + p] = 0.0;
+  }
+}
+
 template <int BN, int STAGES, int MODE>
 pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
   using C = TcCfg<BN, MODE != 0>;
@@ -263,10 +320,23 @@ pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream
   const int m_tiles = (c->n + BM - 1) / BM;
   const int n_tiles = (B + BN - 1) / BN;
   const int tiles = m_tiles * n_tiles;
-  const int grid = tiles < c->num_sms ? tiles : c->num_sms;
   const int num_kb = (c->n + C::K_ELEMS - 1) / C::K_ELEMS;
-  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, num_kb, u,
-                                accumulate ? 1 : 0, c->row_scale,
+  int grid, dp_tiles;
+  if (!c->gemm_streamk || tiles % c->num_sms == 0) {
+    grid = tiles < c->num_sms ? tiles : c->num_sms;
+    dp_tiles = tiles;
+  } else {
+    grid = c->num_sms;
+    dp_tiles = tiles < grid ? 0 : (tiles / grid - 1) * grid;
+  }
+  const long long sk_units = (long long)(tiles - dp_tiles) * num_kb;
+  if (sk_units > 0 && !accumulate) {
+    zero_tiles_kernel<<<tiles - dp_tiles, 256, 0, st>>>(u, c->n, B, BM, BN, n_tiles, dp_tiles,
+                                                         c->flags);
+    PIDE_CUDA_TRY(cudaGetLastError());
+  }
+  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, num_kb, dp_tiles, sk_units,
+                                u, accumulate ? 1 : 0, c->row_scale,
                                 MODE != 0 ? c->col_scale : nullptr, c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
