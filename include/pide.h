@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct pide_ctx* pide_handle;
+typedef struct pide_batch* pide_batch_handle;
 
 typedef enum {
   PIDE_OK = 0,
@@ -175,13 +176,29 @@ pide_status pide_apply_backward(pide_handle h, const double* gout_dev, const dou
                                 int32_t B, int32_t max_sweeps, void* stream);
 
 /*
- * pide_apply_batched -- pide_apply for nprob independent problems (handles
- * of any grid size and format FP32/BF16) with ragged column counts Bs[k], in
- * ONE persistent launch per phase (apply, residual) over a device work list
- * of (problem, row tile) items.  b[k], u[k] are device pointers [Bs[k]][n_k].
- * All handles must live on the current device.  sweeps as in pide_apply
- * (fixed count, tol not supported).
+ * Batched apply (not in the paper; the many-problem form of step 3): nprob
+ * independent problems -- handles of any grid size with FP32 or BF16 stores --
+ * each with its own column count Bs[k] and device buffers b[k], u[k]
+ * ([Bs[k]][n_k] float64).  A plan uploads one problem table and two device
+ * work lists: (problem, 64-row tile, 64-column tile) items, largest first,
+ * for the apply, and (problem, column) items for the right-hand-side prep and
+ * the FP64 residual.  Each phase of the refinement then runs as ONE launch
+ * over all problems: 2 + 2*sweeps launches per run.
+ *
+ * pide_batch_create  builds the plan (allocates; synchronous).  Handles must
+ *                    outlive the plan and share one device; b/u pointers are
+ *                    fixed in the plan.  EUNSUPPORTED for FP64/FP8 stores.
+ * pide_batch_run     enqueues one refined batched apply with `sweeps` sweeps.
+ *                    use_graph != 0 (and a non-NULL stream): the launches are
+ *                    captured into a CUDA graph on the first run with a given
+ *                    sweep count and replayed after that.
+ * pide_batch_destroy releases the plan (synchronises the device).
+ * pide_apply_batched create + run + synchronise + destroy in one call.
  */
+pide_status pide_batch_create(const pide_handle* hs, int32_t nprob, const double* const* b,
+                              double* const* u, const int32_t* Bs, pide_batch_handle* out);
+pide_status pide_batch_run(pide_batch_handle p, int32_t sweeps, int32_t use_graph, void* stream);
+void pide_batch_destroy(pide_batch_handle p);
 pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob, const double* const* b,
                                double* const* u, const int32_t* Bs, int32_t sweeps,
                                void* stream);

@@ -59,6 +59,9 @@ _SIGS = {
     "pide_rhs_from_charge": (_I, [_P, _P, _P, _I, _P]),
     "pide_apply_backward": (_I, [_P, _P, _P, _P, _P, _P, _I, _I, _P]),
     "pide_apply_batched": (_I, [_P, _I, _P, _P, _P, _I, _P]),
+    "pide_batch_create": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_P)]),
+    "pide_batch_run": (_I, [_P, _I, _I, _P]),
+    "pide_batch_destroy": (None, [_P]),
     "pide_reserve": (_I, [_P, _I]),
     "pide_save": (_I, [_P, ctypes.c_char_p]),
     "pide_load": (_I, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
@@ -302,6 +305,38 @@ def apply_batched(solvers, bs, us, sweeps: int = 2, stream=None):
     Bs = (ctypes.c_int32 * k)(*[b.reshape(-1, s.n).shape[0] for b, s in zip(bs, solvers)])
     _check(lib.pide_apply_batched(hs, k, bp, up, Bs, int(sweeps), _stream(stream)),
            "pide_apply_batched")
+
+
+class BatchPlan:
+    """pide_batch_create / run / destroy: the uneven-grid batched apply with
+    optional CUDA-graph replay (buffers are fixed in the plan)."""
+
+    def __init__(self, solvers, bs, us):
+        self.lib = load_library()
+        k = len(solvers)
+        self._keep = (solvers, bs, us)
+        hs = (ctypes.c_void_p * k)(*[s.handle.value for s in solvers])
+        bp = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
+        up = (ctypes.c_void_p * k)(*[u.data_ptr() for u in us])
+        Bs = (ctypes.c_int32 * k)(*[b.reshape(-1, s.n).shape[0] for b, s in zip(bs, solvers)])
+        out = ctypes.c_void_p()
+        _check(self.lib.pide_batch_create(hs, k, bp, up, Bs, ctypes.byref(out)), "pide_batch_create")
+        self.plan = out
+
+    def run(self, sweeps: int = 2, use_graph: bool = True, stream=None):
+        _check(self.lib.pide_batch_run(self.plan, int(sweeps), 1 if use_graph else 0,
+                                       _stream(stream)), "pide_batch_run")
+
+    def close(self):
+        if getattr(self, "plan", None):
+            self.lib.pide_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def header_symbols(header: str | None = None):

@@ -48,3 +48,45 @@ def test_batched_config_sizes():
     precs = ["bf16" if k % 2 else "fp32" for k in range(8)]
     errs = _run(sides, Bs, precs, 8, seed=10)
     assert max(errs) < 1e-6, errs
+
+
+def test_batch_plan_graph_replay():
+    """A plan replayed from its captured CUDA graph gives the same result as
+    direct launches, run after run, and matches the oracle."""
+    from paper_1602_00001_gb300.binding import Solver, BatchPlan
+    sides, Bs = [14, 26, 40, 19], [3, 64, 9, 33]
+    solvers, bs, us, refs = [], [], [], []
+    for k, (side, B) in enumerate(zip(sides, Bs)):
+        h = 1.0 / (side - 1)
+        eps = W.eps_lognormal(side, side, seed=70 + k)
+        b = O.rhs_from_charge(side, side, h, eps, W.gaussian_blobs(side, side, h, 80 + k, batch=B))
+        solvers.append(Solver(side, side, h, eps, "bf16" if k % 2 else "fp32"))
+        bs.append(torch.from_numpy(b).cuda())
+        us.append(torch.zeros_like(bs[-1]))
+        refs.append(O.solve(side, side, eps, b))
+    plan = BatchPlan(solvers, bs, us)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan.run(sweeps=8, use_graph=False, stream=stream)
+    stream.synchronize()
+    direct = [u.clone() for u in us]
+    for _ in range(2):
+        for u in us:
+            u.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            plan.run(sweeps=8, use_graph=True, stream=stream)
+        stream.synchronize()
+        for u, d in zip(us, direct):
+            assert torch.equal(u, d)
+    for u, r in zip(us, refs):
+        assert O.rel_error_eq6(u.cpu().numpy(), r) < 1e-6
+    plan.close()
+
+
+def test_batched_rejects_fp64_store():
+    from paper_1602_00001_gb300.binding import Solver, BatchPlan, PideError
+    s = Solver(10, 10, 1 / 9, None, "fp64")
+    b = torch.zeros((2, s.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(PideError):
+        BatchPlan([s], [b], [torch.empty_like(b)])
