@@ -105,7 +105,9 @@ typedef struct {
  *             quantised; the FP64 copy is kept only for PIDE_FP64.
  *   stream    cudaStream_t for all setup work (the call synchronises it).
  *   out       receives the new handle (NULL on failure).
- * Errors: EINVAL (bad grid, eps), ENOMEM, ECUDA, EUNSUPPORTED (no sm_100+).
+ * Errors: EINVAL (bad grid, eps), ENOMEM, ECUDA, EUNSUPPORTED (not sm_103).
+ * Environment: PIDE_FAULT_ALLOC=1 makes the call fail with ENOMEM before any
+ * device work (host-side fault injection for tests).
  */
 pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
                        void* stream, pide_handle* out);
@@ -241,6 +243,13 @@ typedef enum {
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);
+
+/* Fault-handling self test (no fault is raised): one GPU thread waits on a
+ * barrier that nothing completes, with a budget of budget_cycles SM cycles
+ * (1 .. 2e9).  The bounded wait gives up, the kernel returns, and the call
+ * reports PIDE_ETIMEOUT with the device context intact -- the same path every
+ * kernel's mbarrier waits take. */
+pide_status pide_selftest_wait_timeout(int64_t budget_cycles, void* stream);
 
 const char* pide_status_string(pide_status s);
 const char* pide_last_error(void);

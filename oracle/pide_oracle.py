@@ -495,3 +495,27 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
 def round_fp32(x: np.ndarray) -> np.ndarray:
     """float32 value of each entry (24 significant bits; normal range only)."""
     return round_to_bits(x, 24)
+
+
+def round_e4m3(x: np.ndarray) -> np.ndarray:
+    """e4m3 (OCP FP8, 4 exponent bits, 3 mantissa bits, bias 7) value of each
+    entry, nearest with ties to even, saturating at the largest finite 448:
+    4 significant bits for |x| >= 2^-6, fixed quantum 2^-9 below (subnormals)."""
+    x = np.asarray(x, dtype=np.float64)
+    normal = round_to_bits(x, 4)
+    sub = np.rint(x / 2.0 ** -9) * 2.0 ** -9
+    out = np.where(np.abs(x) >= 2.0 ** -6, normal, sub)
+    return np.clip(out, -448.0, 448.0)
+
+
+def quantize_rows_e4m3(M: np.ndarray, two_terms: bool):
+    """Per-row e4m3 storage of a matrix, the GPU's FP8 format written out:
+    scale s_p = float32(max_q |M_pq| / 448); x = M / s in FP64, taken to
+    float32, hi = e4m3(x); lo = e4m3(float32(x - hi)).  Returns (s, hi, lo)
+    with lo = 0 when two_terms is False."""
+    mx = np.max(np.abs(M), axis=1)
+    s = round_fp32(np.where(mx > 0, mx / 448.0, 1.0))
+    x = M * (1.0 / s)[:, None]
+    hi = round_e4m3(round_fp32(x))
+    lo = round_e4m3(round_fp32(x - hi)) if two_terms else np.zeros_like(hi)
+    return s, hi, lo

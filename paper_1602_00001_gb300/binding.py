@@ -71,6 +71,7 @@ _SIGS = {
     "pide_get_inverse_row": (_I, [_P, _I, _P]),
     "pide_set_tuning": (_I, [_P, _I, _I]),
     "pide_get_tuning": (_I, [_P, _I, ctypes.POINTER(_I)]),
+    "pide_selftest_wait_timeout": (_I, [ctypes.c_int64, _P]),
     "pide_status_string": (ctypes.c_char_p, [_I]),
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -282,6 +283,21 @@ extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pi
   if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 4) {
     set_error("pide_setup: bad argument");
     return PIDE_EINVAL;
+  }
+  if (eps_host) {
+    const size_t N = (size_t)g->nx * g->ny;
+    for (size_t k = 0; k < N; ++k)
+      if (!std::isfinite(eps_host[k]) || !(eps_host[k] > 0.0)) {
+        set_error("eps must be finite and > 0 at every node");
+        return PIDE_EINVAL;
+      }
+  }
+  // host-side fault injection for tests: pretend the device allocation failed
+  if (const char* f = std::getenv("PIDE_FAULT_ALLOC")) {
+    if (f[0] == '1') {
+      set_error("PIDE_FAULT_ALLOC=1: injected allocation failure");
+      return PIDE_ENOMEM;
+    }
   }
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = (cudaStream_t)stream;
@@ -719,6 +735,42 @@ extern "C" const char* pide_status_string(pide_status s) {
     case PIDE_EUNSUPPORTED: return "unsupported";
   }
   return "unknown status";
+}
+
+// One thread waits on an mbarrier that nothing will complete, with a short
+// cycle budget: the bounded-wait path every kernel uses gives up, records the
+// error word and returns, and the host reports PIDE_ETIMEOUT.
+__global__ void timeout_probe_kernel(long long budget, uint32_t* flags) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_s;
+  mbar_init(&bar, 1);
+  abort_s = 0;
+  fence_barrier_init();
+  if (!mbar_wait_bounded(&bar, 0, &abort_s, budget)) flags[FLAG_ERROR] = DEV_TIMEOUT_MMA;
+  mbar_arrive(&bar);   // complete the phase so nothing is left pending
+}
+
+extern "C" pide_status pide_selftest_wait_timeout(int64_t budget_cycles, void* stream) {
+  if (budget_cycles <= 0 || budget_cycles > (int64_t)PIDE_WAIT_BUDGET_CYCLES) {
+    set_error("pide_selftest_wait_timeout: budget out of range");
+    return PIDE_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* fl = nullptr;
+  PIDE_CUDA_TRY(cudaMalloc((void**)&fl, FLAG_COUNT * sizeof(uint32_t)));
+  cudaMemsetAsync(fl, 0, FLAG_COUNT * sizeof(uint32_t), st);
+  timeout_probe_kernel<<<1, 1, 0, st>>>((long long)budget_cycles, fl);
+  cudaError_t e = cudaGetLastError();
+  uint32_t code = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&code, fl + FLAG_ERROR, sizeof(code), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(fl);
+  PIDE_CUDA_TRY(e);
+  if (code) {
+    set_error("bounded wait expired as requested (code " + std::to_string(code) + ")");
+    return PIDE_ETIMEOUT;
+  }
+  return PIDE_OK;
 }
 
 extern "C" const char* pide_last_error(void) { return g_last_error.c_str(); }

@@ -188,13 +188,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait: returns false (and leaves the barrier alone) once the cycle
 // budget is spent or *abort becomes non-zero.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  volatile int* abort_flag) {
+                                                  volatile int* abort_flag,
+                                                  long long budget = PIDE_WAIT_BUDGET_CYCLES) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > PIDE_WAIT_BUDGET_CYCLES) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 

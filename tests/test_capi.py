@@ -68,3 +68,19 @@ def test_oracle_binary_rounding_pins():
     # ties to even: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> 1
     assert O.round_bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
     assert O.round_bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+
+
+def test_oracle_e4m3_rounding_pins():
+    """round_e4m3 against torch's float8_e4m3fn conversion of float32 values
+    (normal and subnormal range, ties), inside the finite range."""
+    import torch
+    rng = np.random.default_rng(1)
+    x = (rng.standard_normal(6000) * 10.0 ** rng.uniform(-4, 2.6, 6000)).astype(np.float32)
+    x = np.clip(x, -448, 448).astype(np.float64)
+    ref = torch.from_numpy(x).to(torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(O.round_e4m3(x), ref)
+    # exact grid points and halfway cases: 1.0625 is halfway between 1 and 1.125 -> 1
+    assert O.round_e4m3(np.array([1.0625]))[0] == 1.0
+    assert O.round_e4m3(np.array([1.1875]))[0] == 1.25
+    assert O.round_e4m3(np.array([2.0 ** -10]))[0] == 0.0          # ties to even at the bottom
+    assert O.round_e4m3(np.array([3 * 2.0 ** -10]))[0] == 2.0 ** -8

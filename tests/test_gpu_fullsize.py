@@ -46,12 +46,15 @@ def test_refined_bf16_full_size(problem):
     # B = 1 takes the GEMV path
     u1 = s.apply(bd[:1], sweeps=SWEEPS)
     assert O.rel_error_eq6(u1.cpu().numpy(), ref[:1]) < 1e-6
-    # whole-tile and stream-K schedules agree
+    # whole-tile and stream-K schedules agree up to FP32 partial-sum rounding,
+    # bounded elementwise by the contraction of magnitudes; L^-1 >= 0 (an
+    # M-matrix inverse), so that is the apply of |b|
     s.set_tuning(gemm_streamk=0)
     u0 = s.apply(bd, sweeps=0)
     s.set_tuning(gemm_streamk=1)
     uk = s.apply(bd, sweeps=0)
-    assert (u0 - uk).abs().max().item() <= 1e-5 * u0.abs().max().item()
+    mag = s.apply(bd.abs(), sweeps=0)
+    assert bool(((u0 - uk).abs() <= 2e-5 * mag + 1e-300).all())
     s.close()
 
 

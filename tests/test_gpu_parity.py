@@ -216,7 +216,73 @@ def test_streamk_matches_whole_tiles(B):
     b = _b(nx, ny, h, eps, B, seed=22)
     s = _solver(nx, ny, h, eps, "bf16")
     s.set_tuning(gemm_streamk=1)
-    u1 = s.apply(b, sweeps=1).cpu().numpy()
+    u1 = s.apply(b, sweeps=0).cpu().numpy()
     s.set_tuning(gemm_streamk=0)
-    u0 = s.apply(b, sweeps=1).cpu().numpy()
-    assert np.max(np.abs(u1 - u0)) <= 1e-5 * np.max(np.abs(u0))
+    u0 = s.apply(b, sweeps=0).cpu().numpy()
+    mag = s.apply(np.abs(b), sweeps=0).cpu().numpy()     # L^-1 >= 0: the |.| contraction
+    assert np.all(np.abs(u1 - u0) <= 2e-5 * mag + 1e-300)
+
+
+@pytest.mark.parametrize("prec", ["fp8x2", "fp8"])
+@pytest.mark.parametrize("B", [16, 64, 300])
+def test_fp8_single_apply_is_exact_contraction(prec, B):
+    """kind::f8f6f4 GEMM: one apply equals the FP64 contraction of the
+    oracle's own e4m3 rounding of the inverse (per-row scale, hi [+ lo]) and
+    of the right-hand side (per-column scale), up to FP32 accumulation."""
+    nx, ny = 40, 33
+    h = 1.0 / 39
+    eps = W.eps_fourier(nx, ny, h, seed=11)
+    b = _b(nx, ny, h, eps, B, seed=B + 7)
+    s = _solver(nx, ny, h, eps, prec)
+    u = s.apply(b, sweeps=0).cpu().numpy()
+    Linv = O.interior_inverse(nx, ny, eps)
+    rs, hi, lo = O.quantize_rows_e4m3(Linv, prec == "fp8x2")
+    Q = hi + lo
+    t = O.round_fp32(np.max(np.abs(b), axis=1) / 448.0)
+    isc = O.round_fp32(1.0 / t)
+    r = O.round_e4m3(O.round_fp32(b * isc[:, None]))
+    ref = (rs[:, None] * (Q @ r.T)).T * t[:, None]
+    mag = (rs[:, None] * (np.abs(Q) @ np.abs(r).T)).T * t[:, None]
+    err = np.abs(u - ref)
+    assert np.all(err <= 2e-5 * mag + 1e-300), float(np.max(err / mag))
+    # the stored rows the library reports are scale * (hi + lo)
+    row = s.inverse_row(3)
+    assert np.max(np.abs(row - rs[3] * Q[3])) <= 1e-6 * np.max(np.abs(Q[3])) * rs[3]
+
+
+@pytest.mark.parametrize("B", [1, 64, 300])
+def test_fp8x2_refined_reaches_1e6(B):
+    nx = ny = 50
+    h = 1.0 / 49
+    eps = W.eps_fourier(nx, ny, h, seed=1)
+    b = _b(nx, ny, h, eps, B, seed=300 + B)
+    s = _solver(nx, ny, h, eps, "fp8x2")
+    u = s.apply(b, sweeps=10)
+    ref = O.solve(nx, ny, eps, b, route="band")
+    assert O.rel_error_eq6(u.cpu().numpy(), ref) < 1e-6
+
+
+def test_apply_in_cuda_graph():
+    """The refined apply (prep, GEMM, residual sweeps) captured once in a CUDA
+    graph and replayed gives the eager result."""
+    nx = ny = 44
+    h = 1.0 / 43
+    eps = W.eps_lognormal(nx, ny, seed=31)
+    b = torch.from_numpy(_b(nx, ny, h, eps, 96, seed=32)).cuda()
+    s = _solver(nx, ny, h, eps, "bf16")
+    s.set_tuning(gemm_streamk=0)          # whole tiles: bitwise-repeatable
+    s.reserve(96)
+    u_eager = s.apply(b, sweeps=4)
+    u = torch.zeros_like(b)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        s.apply(b, u, sweeps=4, stream=st)          # warm-up outside capture
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        s.apply(b, u, sweeps=4, stream=st)
+    u.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(u, u_eager)
