@@ -96,6 +96,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x: float, dist=None) -> float:
+    """Max over ranks of a per-rank time (gloo: CPU tensor; nccl: CUDA tensor)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, per_rank_batch: int, steps: int, ms_total_max: float) -> float:
+    """Right-hand sides solved by all ranks per second of the slowest rank."""
+    return world * per_rank_batch * steps / (ms_total_max / 1e3)
+
+
 def cpu_oracle_rate(nx, ny, h, eps, b_np, cols, factor=None):
     """Oracle (numpy band LU) solves/s on a bounded sample of columns.
     Returns (solves_per_s, seconds, factor_object, solution)."""
@@ -264,12 +280,10 @@ def main():
             torch.cuda.synchronize()
         ms_total = e0.elapsed_time(e1_)
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = reduce_max(ms_total, dist)
         dist.barrier()
     ms_step = ms_total / args.steps
-    value = world * B * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(world, B, args.steps, ms_total)
     err_final = err_of(u)
 
     # B = 1 rate
@@ -285,10 +299,7 @@ def main():
     for _ in range(e2e_steps):
         s.apply_host(b_host, u_host, sweeps=k)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(e2e_s, dist)
     e2e_value = world * B / e2e_s
 
     # ---- roofline of the dominant kernel (the apply GEMM), from live CUDA events

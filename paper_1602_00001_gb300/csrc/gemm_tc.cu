@@ -54,14 +54,28 @@ struct TcCfg {
   static constexpr uint32_t TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
 };
 
-// The (tile, k-block range) segments one CTA works through, identical for all roles.
+// The (tile, k-block range) segments one CTA works through, identical for all
+// roles.  Data-parallel part: tiles blockIdx.x, +G, ... below dp_tiles.
+// Stream-K part: the remaining 128-row slabs x k-blocks are split evenly over
+// groups of T = n_tiles consecutive CTAs; the T CTAs of a group walk the same
+// (slab, k-range) in lockstep, one right-hand-side tile each, so every slab
+// of the inverse is still fetched from HBM about once.
 struct SegIter {
-  int G, dp_tiles, num_kb, t_dp;
+  int G, T, dp_tiles, num_kb, t_dp, j, base_m;
   long long u, u1;
-  __device__ SegIter(int dp, int nkb, long long sk_units)
-      : G((int)gridDim.x), dp_tiles(dp), num_kb(nkb), t_dp((int)blockIdx.x) {
-    u = sk_units * blockIdx.x / gridDim.x;
-    u1 = sk_units * (blockIdx.x + 1) / gridDim.x;
+  __device__ SegIter(int dp, int nkb, int n_tiles, int m_tiles, int sk)
+      : G((int)gridDim.x), T(n_tiles), dp_tiles(dp), num_kb(nkb), t_dp((int)blockIdx.x) {
+    const int NG = G / T;
+    const int g = (int)blockIdx.x / T;
+    j = (int)blockIdx.x - g * T;
+    base_m = dp_tiles / T;
+    const long long U = sk ? (long long)(m_tiles - base_m) * nkb : 0;
+    if (NG > 0 && g < NG) {
+      u = U * g / NG;
+      u1 = U * (g + 1) / NG;
+    } else {
+      u = u1 = 0;
+    }
   }
   __device__ bool next(int& tile, int& kb0, int& kb1) {
     if (t_dp < dp_tiles) {
@@ -72,7 +86,8 @@ struct SegIter {
       return true;
     }
     if (u < u1) {
-      tile = dp_tiles + (int)(u / num_kb);
+      const int m = base_m + (int)(u / num_kb);
+      tile = m * T + j;
       kb0 = (int)(u % num_kb);
       const long long left = u1 - u;
       kb1 = (kb0 + left < num_kb) ? kb0 + (int)left : num_kb;
@@ -87,7 +102,7 @@ template <int BN, int STAGES, int MODE>   // MODE 0: BF16, 1: FP8 (hi only), 2: 
 __global__ void __launch_bounds__(192, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
                const __grid_constant__ CUtensorMap tmR, int n, int B, int num_kb, int dp_tiles,
-               long long sk_units, double* __restrict__ u, int accumulate,
+               int sk, double* __restrict__ u, int accumulate,
                const float* __restrict__ row_scale, const float* __restrict__ col_scale,
                uint32_t* __restrict__ flags) {
   constexpr bool FP8 = MODE != 0;
@@ -112,6 +127,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = (B + BN - 1) / BN;
+  const int m_tiles = (n + BM - 1) / BM;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -147,7 +163,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint32_t issued = 0;                            // bit s: stage s has a copy in flight
     uint32_t issued_ph = 0;                         // parity of that copy's phase
     bool ok = true;
-    SegIter it(dp_tiles, num_kb, sk_units);
+    SegIter it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
     int tile, kb0, kb1;
     while (ok && it.next(tile, kb0, kb1)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
@@ -189,7 +205,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     int acc = 0;
     uint32_t acc_ph = 0;
     bool ok = true;
-    SegIter it(dp_tiles, num_kb, sk_units);
+    SegIter it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
     int tile, kb0, kb1;
     while (ok && it.next(tile, kb0, kb1)) {
       if (!mbar_wait_bounded(&tempty[acc], acc_ph ^ 1, abort_s)) {
@@ -243,7 +259,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int row_in_tile = quarter * 32 + lane;
     int acc = 0;
     uint32_t acc_ph = 0;
-    SegIter it(dp_tiles, num_kb, sk_units);
+    SegIter it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
     int tile, kb0, kb1;
     while (it.next(tile, kb0, kb1)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
@@ -322,20 +338,21 @@ pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream
   const int tiles = m_tiles * n_tiles;
   const int num_kb = (c->n + C::K_ELEMS - 1) / C::K_ELEMS;
   int grid, dp_tiles;
-  if (!c->gemm_streamk || tiles % c->num_sms == 0) {
+  if (!c->gemm_streamk || tiles % c->num_sms == 0 || n_tiles > c->num_sms) {
     grid = tiles < c->num_sms ? tiles : c->num_sms;
     dp_tiles = tiles;
   } else {
+    // all but the last one-and-a-bit waves whole; dp_tiles a whole number of slabs
     grid = c->num_sms;
-    dp_tiles = tiles < grid ? 0 : (tiles / grid - 1) * grid;
+    dp_tiles = tiles < grid ? 0 : ((tiles / grid - 1) * grid / n_tiles) * n_tiles;
   }
-  const long long sk_units = (long long)(tiles - dp_tiles) * num_kb;
-  if (sk_units > 0 && !accumulate) {
+  const int sk = dp_tiles < tiles ? 1 : 0;
+  if (sk && !accumulate) {
     zero_tiles_kernel<<<tiles - dp_tiles, 256, 0, st>>>(u, c->n, B, BM, BN, n_tiles, dp_tiles,
                                                          c->flags);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
-  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, num_kb, dp_tiles, sk_units,
+  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, num_kb, dp_tiles, sk,
                                 u, accumulate ? 1 : 0, c->row_scale,
                                 MODE != 0 ? c->col_scale : nullptr, c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());

@@ -48,13 +48,15 @@ def test_refined_bf16_full_size(problem):
     assert O.rel_error_eq6(u1.cpu().numpy(), ref[:1]) < 1e-6
     # whole-tile and stream-K schedules agree up to FP32 partial-sum rounding,
     # bounded elementwise by the contraction of magnitudes; L^-1 >= 0 (an
-    # M-matrix inverse), so that is the apply of |b|
+    # M-matrix inverse), so that is the apply of |b|.  K = 39204 is 2450
+    # MMA steps of K = 16; their FP32 accumulation can differ by up to
+    # ~2450 * 2^-24 = 1.5e-4 of the magnitude; 1e-4 is the bound used.
     s.set_tuning(gemm_streamk=0)
     u0 = s.apply(bd, sweeps=0)
     s.set_tuning(gemm_streamk=1)
     uk = s.apply(bd, sweeps=0)
     mag = s.apply(bd.abs(), sweeps=0)
-    assert bool(((u0 - uk).abs() <= 2e-5 * mag + 1e-300).all())
+    assert bool(((u0 - uk).abs() <= 1e-4 * mag + 1e-300).all())
     s.close()
 
 

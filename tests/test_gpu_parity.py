@@ -119,18 +119,22 @@ def _oracle_lowprec_apply(nx, ny, eps, b, store_round, rhs_round):
 @pytest.mark.parametrize("B", [1, 3, 8, 9, 40, 64, 65, 130, 300])
 def test_bf16_single_apply_is_exact_contraction(B):
     """One apply (no refinement) equals the FP64 contraction of the same
-    bf16-rounded inverse and right-hand side up to FP32 accumulation; B <= 8
-    takes the GEMV (FP32 right-hand side), larger B the tcgen05 GEMM."""
+    bf16-rounded inverse and right-hand side up to FP32 accumulation.  B up
+    to the GEMV limit (default 1) takes the GEMV (FP32 right-hand side),
+    larger B the tcgen05 GEMM (BF16 right-hand side); B <= 8 is checked on
+    both by moving the limit."""
     nx, ny = 40, 33
     h = 1.0 / 39
     eps = W.eps_fourier(nx, ny, h, seed=11)
     b = _b(nx, ny, h, eps, B, seed=B)
     s = _solver(nx, ny, h, eps, "bf16")
-    u = s.apply(b, sweeps=0).cpu().numpy()
-    rhs_round = O.round_fp32 if B <= 8 else O.round_bf16
-    ref, mag = _oracle_lowprec_apply(nx, ny, eps, b, O.round_bf16, rhs_round)
-    err = np.abs(u - ref)
-    assert np.all(err <= 2e-5 * mag + 1e-300), float(np.max(err / mag))
+    for limit in ([1, 8] if B <= 8 else [1]):
+        s.set_tuning(gemv_max_b=limit)
+        u = s.apply(b, sweeps=0).cpu().numpy()
+        rhs_round = O.round_fp32 if B <= limit else O.round_bf16
+        ref, mag = _oracle_lowprec_apply(nx, ny, eps, b, O.round_bf16, rhs_round)
+        err = np.abs(u - ref)
+        assert np.all(err <= 2e-5 * mag + 1e-300), (limit, float(np.max(err / mag)))
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
