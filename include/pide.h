@@ -233,13 +233,18 @@ pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
  *   PIDE_TUNE_GEMV_MAX_B    largest B served by the GEMV instead of the GEMM: 1..8 (default 1)
  *   PIDE_TUNE_GEMM_BN       tensor-core tile width for B > 128: 128 or 256 (default 256)
  *   PIDE_TUNE_GEMM_STREAMK  1: split the last partial wave of tiles over all SMs by
- *                           k-blocks (FP64 atomic partial sums); 0: whole tiles only */
+ *                           k-blocks (FP64 atomic partial sums); 0: whole tiles only
+ *   PIDE_TUNE_OVERLAP       1 (default): for B >= 512 with tol <= 0, split the columns in
+ *                           two groups and run each group's FP64 residual on a
+ *                           low-priority internal stream under the other group's
+ *                           tensor-core apply; 0: one stream, whole batch per phase */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
   PIDE_TUNE_GEMV_MAX_B = 2,
   PIDE_TUNE_GEMM_BN = 3,
-  PIDE_TUNE_GEMM_STREAMK = 4
+  PIDE_TUNE_GEMM_STREAMK = 4,
+  PIDE_TUNE_OVERLAP = 5
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -141,12 +141,50 @@ pide_status ensure_workspace(pide_ctx* c, int B) {
 
 // ---------------------------------------------------------------- apply
 
-pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                         int col0) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 0);
-  if (B <= c->gemv_max_b) return launch_gemv(c, B, u, accumulate, st);
-  if (c->prec == PIDE_FP64 || c->prec == PIDE_FP32) return launch_gemm_simt(c, B, u, accumulate, st);
-  return launch_gemm_tc(c, B, u, accumulate, st);
+  if (col0 == 0 && B <= c->gemv_max_b) return launch_gemv(c, B, u, accumulate, st);
+  if (col0 == 0 && (c->prec == PIDE_FP64 || c->prec == PIDE_FP32))
+    return launch_gemm_simt(c, B, u, accumulate, st);
+  return launch_gemm_tc(c, B, u + (size_t)col0 * c->n, accumulate, st, col0);
+}
+
+// Refinement with the FP64 residual of one column group hidden under the
+// tensor-core apply of the other.  Columns split into groups A = [0, Ba) and
+// B = [Ba, B).  Main stream: apply(A), apply(B), apply(A), ...; aux stream
+// (lower priority): residual(A) after apply(A), residual(B) after apply(B).
+// The residual runs on the FP64 pipe and the apply on the tensor pipe, so
+// they share the SMs with little interference.  Events fork the aux stream
+// from the caller's stream and join it back (graph-capturable).
+static pide_status solve_overlapped(pide_ctx* c, const double* b, int mode, const double* lift,
+                                    double* x, int B, int sweeps, int rf, cudaStream_t st) {
+  const int Ba = ((B / 2 + 127) / 128) * 128;
+  const int Bb = B - Ba;
+  const int g0[2] = {0, Ba}, gn[2] = {Ba, Bb};
+  cudaEvent_t fork = c->ev[0], appl[2] = {c->ev[1], c->ev[2]}, res = c->ev[3];
+  PIDE_CUDA_TRY(cudaEventRecord(fork, st));
+  PIDE_CUDA_TRY(cudaStreamWaitEvent(c->aux, fork, 0));
+  if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
+  PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, false, st));
+  for (int k = 0; k <= sweeps; ++k) {
+    for (int g = 0; g < 2; ++g) {
+      if (k > 0) PIDE_CUDA_TRY(cudaStreamWaitEvent(st, c->ev[4 + g], 0));
+      PIDE_TRY(launch_apply(c, gn[g], x, k > 0, st, g0[g]));
+      if (k == sweeps) continue;
+      PIDE_CUDA_TRY(cudaEventRecord(appl[g], st));
+      PIDE_CUDA_TRY(cudaStreamWaitEvent(c->aux, appl[g], 0));
+      if (rf == RF_E4M3)
+        PIDE_TRY(launch_fp8_scales(c, b, x, gn[g], mode, lift, true, c->aux, g0[g]));
+      PIDE_TRY(launch_residual(c, b, x, gn[g], mode, lift, rf, true, nullptr, false, true, c->aux,
+                               g0[g]));
+      PIDE_CUDA_TRY(cudaEventRecord(c->ev[4 + g], c->aux));
+    }
+  }
+  PIDE_CUDA_TRY(cudaEventRecord(res, c->aux));
+  PIDE_CUDA_TRY(cudaStreamWaitEvent(st, res, 0));
+  return PIDE_OK;
 }
 
 // L x = f with x = Q(L^-1) q(f), then `sweeps` refinement sweeps
@@ -158,6 +196,10 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
   PIDE_CUDA_TRY(cudaMemsetAsync(c->flags, 0, FLAG_COUNT * sizeof(uint32_t), st));
   PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, 3 * (size_t)c->ws_B * sizeof(double), st));
   const int rf = rhs_format(c, B);
+  const bool tensor = B > c->gemv_max_b && (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 ||
+                                            c->prec == PIDE_FP8X2);
+  if (c->overlap && tensor && tol <= 0 && sweeps > 0 && B >= 512 && c->aux)
+    return solve_overlapped(c, b, mode, lift, x, B, sweeps, rf, st);
   if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
   PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
@@ -271,6 +313,10 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->lift, (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->flags, FLAG_COUNT * sizeof(uint32_t)));
   PIDE_CUDA_TRY(cudaMemset(c->flags, 0, FLAG_COUNT * sizeof(uint32_t)));
+  int prio_lo = 0, prio_hi = 0;
+  PIDE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  PIDE_CUDA_TRY(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_lo));
+  for (int k = 0; k < 6; ++k) PIDE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
   PIDE_CUDA_TRY(cudaMemcpyAsync(c->eps, c->eps_host.data(), N * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
   PIDE_TRY(launch_assemble(c, st));
@@ -357,6 +403,9 @@ extern "C" void pide_destroy(pide_handle h) {
     cudaEventDestroy(ev.a);
     cudaEventDestroy(ev.b);
   }
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->aux) cudaStreamDestroy(h->aux);
   delete h;
 }
 
@@ -703,6 +752,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 0 && value != 1) break;
       h->gemm_streamk = value;
       return PIDE_OK;
+    case PIDE_TUNE_OVERLAP:
+      if (value != 0 && value != 1) break;
+      h->overlap = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -719,6 +772,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_GEMV_MAX_B: *value = h->gemv_max_b; return PIDE_OK;
     case PIDE_TUNE_GEMM_BN: *value = h->gemm_bn_large; return PIDE_OK;
     case PIDE_TUNE_GEMM_STREAMK: *value = h->gemm_streamk; return PIDE_OK;
+    case PIDE_TUNE_OVERLAP: *value = h->overlap; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

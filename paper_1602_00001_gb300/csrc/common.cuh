@@ -85,6 +85,9 @@ struct pide_ctx {
   // launch-shape knobs (pide_set_tuning; the autotuner sets them)
   int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
   int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
+  int overlap = 1;                  // residual of one column group under the GEMM of the other
+  cudaStream_t aux = nullptr;       // low-priority stream for the overlapped residuals
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
   int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8
@@ -110,22 +113,26 @@ pide_status quantize_store(pide_ctx* c, const double* G, cudaStream_t st);
 pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
                         int rfmt, bool track, cudaStream_t st);
 // Residual: R = q(f - L u) (FP64 stencil); optional column max of |r| into colmax.
+// col0: first column of a column group (b, u, R rows, scales and maxima offset by it).
 pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
-                            bool honor_done, cudaStream_t st);
+                            bool honor_done, cudaStream_t st, int col0 = 0);
 pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
 // FP8 right-hand sides: per-column scale max|f~|/448 (prep) or max|r~|/448 (residual).
 pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int B, int mode,
-                              const double* lift, bool from_residual, cudaStream_t st);
+                              const double* lift, bool from_residual, cudaStream_t st,
+                              int col0 = 0);
 pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const double* lift,
                             cudaStream_t st);
 
 // Apply: u (=|+=) Q(L^-1) R for B columns.
-pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                         int col0 = 0);
 int rhs_format(const pide_ctx* c, int B);   // element format R must hold for this B
 
 // tensor-core GEMM (BF16, FP8X2) and SIMT paths
-pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                           int col0 = 0);
 pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 pide_status launch_gemm_simt(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 

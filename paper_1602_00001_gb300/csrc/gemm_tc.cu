@@ -101,8 +101,8 @@ struct SegIter {
 template <int BN, int STAGES, int MODE>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo)
 __global__ void __launch_bounds__(192, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
-               const __grid_constant__ CUtensorMap tmR, int n, int B, int num_kb, int dp_tiles,
-               int sk, double* __restrict__ u, int accumulate,
+               const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
+               int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                const float* __restrict__ row_scale, const float* __restrict__ col_scale,
                uint32_t* __restrict__ flags) {
   constexpr bool FP8 = MODE != 0;
@@ -176,7 +176,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int kx = kb * C::K_ELEMS;
         tma_load_2d_hint(sA + s * A_STAGE, &tmA, &full[s], kx, mt * BM, pol_a);
         if (LO) tma_load_2d_hint(sA + s * A_STAGE + C::A_BYTES, &tmAlo, &full[s], kx, mt * BM, pol_a);
-        tma_load_2d_hint(sB + s * C::B_BYTES, &tmR, &full[s], kx, nt * BN, pol_r);
+        tma_load_2d_hint(sB + s * C::B_BYTES, &tmR, &full[s], kx, rrow0 + nt * BN, pol_r);
         issued |= 1u << s;
         issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
         if (++s == STAGES) {
@@ -326,7 +326,7 @@ __global__ void zero_tiles_kernel(double* __restrict__ u, int n, int B, int bm, 
 }
 
 template <int BN, int STAGES, int MODE>
-pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st, int col0) {
   using C = TcCfg<BN, MODE != 0>;
   constexpr int A_STAGE = (MODE == 2) ? 2 * C::A_BYTES : C::A_BYTES;
   const size_t smem = 1024 + (size_t)STAGES * (A_STAGE + C::B_BYTES) + 256;
@@ -352,45 +352,47 @@ pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream
                                                          c->flags);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
-  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, num_kb, dp_tiles, sk,
+  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, col0, num_kb, dp_tiles, sk,
                                 u, accumulate ? 1 : 0, c->row_scale,
-                                MODE != 0 ? c->col_scale : nullptr, c->flags);
+                                MODE != 0 ? c->col_scale + col0 : nullptr, c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
 
 template <int MODE>
-pide_status launch_tc_mode(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+pide_status launch_tc_mode(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                           int col0) {
   // BN: the smallest supported tile that covers B (up to 256); stages fill ~200 KB.
   if (MODE == 0) {
-    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st);
-    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st);
-    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st);
-    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st);
+    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0);
+    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st, col0);
   } else if (MODE == 1) {
-    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st);
-    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st);
-    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st);
-    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st);
+    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0);
+    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st, col0);
   } else {
-    if (B <= 32) return launch_tc<32, 6, MODE>(c, B, u, accumulate, st);
-    if (B <= 64) return launch_tc<64, 5, MODE>(c, B, u, accumulate, st);
-    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 4, MODE>(c, B, u, accumulate, st);
-    return launch_tc<256, 3, MODE>(c, B, u, accumulate, st);
+    if (B <= 32) return launch_tc<32, 6, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 64) return launch_tc<64, 5, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 4, MODE>(c, B, u, accumulate, st, col0);
+    return launch_tc<256, 3, MODE>(c, B, u, accumulate, st, col0);
   }
 }
 
 }  // namespace
 
-pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st) {
+pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                           int col0) {
   if (!c->tmA_ok) {
     set_error("tensor-core apply: TMA maps were not created");
     return PIDE_EUNSUPPORTED;
   }
   switch (c->prec) {
-    case PIDE_BF16: return launch_tc_mode<0>(c, B, u, accumulate, st);
-    case PIDE_FP8: return launch_tc_mode<1>(c, B, u, accumulate, st);
-    case PIDE_FP8X2: return launch_tc_mode<2>(c, B, u, accumulate, st);
+    case PIDE_BF16: return launch_tc_mode<0>(c, B, u, accumulate, st, col0);
+    case PIDE_FP8: return launch_tc_mode<1>(c, B, u, accumulate, st, col0);
+    case PIDE_FP8X2: return launch_tc_mode<2>(c, B, u, accumulate, st, col0);
     default: return PIDE_EUNSUPPORTED;
   }
 }

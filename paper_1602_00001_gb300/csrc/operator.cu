@@ -310,19 +310,23 @@ pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const dou
 
 pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
-                            bool honor_done, cudaStream_t st) {
+                            bool honor_done, cudaStream_t st, int col0) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 1);
   dim3 g = col_grid(c->n, B);
-  void* R = write_R ? c->R : nullptr;
+  const size_t off = (size_t)col0 * c->n;
+  b += off;
+  u += off;
+  if (r_out) r_out += off;
+  void* R = write_R ? (void*)((uint8_t*)c->R + (size_t)col0 * c->ld * rhs_elem_bytes(rfmt)) : nullptr;
   const uint32_t* fl = honor_done ? c->flags : nullptr;
-  double* cm = c->colmax;
+  double* cm = c->colmax + col0;
   const int t = track ? 1 : 0;
   switch (rfmt) {
     case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, c->col_scale, r_out, cm, t, fl); break;
+    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -397,11 +401,13 @@ __global__ void finalize_scale_kernel(double* __restrict__ colmax_raw, float* __
 }  // namespace
 
 pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int B, int mode,
-                              const double* lift, bool from_residual, cudaStream_t st) {
+                              const double* lift, bool from_residual, cudaStream_t st, int col0) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 2);
   dim3 g = col_grid(c->n, B);
-  double* raw = c->colmax + 2 * (size_t)c->ws_B;
+  double* raw = c->colmax + 2 * (size_t)c->ws_B + col0;
+  b += (size_t)col0 * c->n;
+  if (u) u += (size_t)col0 * c->n;
   if (from_residual) {
     residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift,
                                                nullptr, nullptr, nullptr, raw, 1, c->flags);
@@ -409,7 +415,7 @@ pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int
     colmax_raw_prep_kernel<<<g, 256, 0, st>>>(b, c->n, mode, c->dinv, lift, raw);
   }
   PIDE_CUDA_TRY(cudaGetLastError());
-  finalize_scale_kernel<<<(B + 255) / 256, 256, 0, st>>>(raw, c->col_scale, B, c->flags);
+  finalize_scale_kernel<<<(B + 255) / 256, 256, 0, st>>>(raw, c->col_scale + col0, B, c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }

@@ -290,3 +290,39 @@ def test_apply_in_cuda_graph():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(u, u_eager)
+
+
+@pytest.mark.parametrize("B", [512, 640])
+def test_overlapped_refinement(B):
+    """Residual of one column group on the aux stream under the other group's
+    apply: same result as the single-stream schedule up to FP32 partial-sum
+    rounding, reaches the oracle, and replays from a captured CUDA graph."""
+    nx = ny = 48
+    h = 1.0 / 47
+    eps = W.eps_fourier(nx, ny, h, seed=41)
+    b_np = _b(nx, ny, h, eps, B, seed=42)
+    b = torch.from_numpy(b_np).cuda()
+    s = _solver(nx, ny, h, eps, "bf16")
+    s.reserve(B)
+    s.set_tuning(overlap=0)
+    u_seq = s.apply(b, sweeps=6)
+    s.set_tuning(overlap=1)
+    u_ovl = s.apply(b, sweeps=6)
+    ref = O.solve(nx, ny, eps, b_np, route="band")
+    assert O.rel_error_eq6(u_ovl.cpu().numpy(), ref) < 1e-6
+    assert float((u_ovl - u_seq).abs().max()) <= 1e-8 * float(u_seq.abs().max())
+    s.set_tuning(gemm_streamk=0)
+    u_eager = s.apply(b, sweeps=6)
+    u = torch.zeros_like(b)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        s.apply(b, u, sweeps=6, stream=st)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        s.apply(b, u, sweeps=6, stream=st)
+    u.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(u, u_eager)
