@@ -205,6 +205,23 @@ pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob, const doubl
                                double* const* u, const int32_t* Bs, int32_t sweeps,
                                void* stream);
 
+/*
+ * pide_apply_noalloc -- pide_apply(h, b, u, B, sweeps, tol = 0, g = NULL)
+ * without any device allocation, for callers that cannot call cudaMalloc
+ * (a fixed memory pool, a real-time loop, a host application that hands out
+ * only pre-sized buffers).  The paper has no counterpart: it is a deployment
+ * variant of step 3.  The caller passes b and u ([B][n] float64, device);
+ * the FP32 scratch right-hand side lives in a fixed array inside the library
+ * (2 MiB, held by every GPU that loads the library until exit), so B <= 8
+ * and n <= 65536, else EINVAL with a message.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) -- make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU race and must be serialised.  Results equal
+ * pide_apply's up to FP32 summation order.
+ */
+pide_status pide_apply_noalloc(pide_handle h, const double* b_dev, double* u_dev, int32_t B,
+                               int32_t sweeps, void* stream);
+
 /* Reserve workspace for up to Bmax columns now, so later pide_apply calls with
  * B <= Bmax allocate nothing (required before capturing them in a CUDA graph). */
 pide_status pide_reserve(pide_handle h, int32_t Bmax);

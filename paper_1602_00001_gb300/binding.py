@@ -63,6 +63,7 @@ _SIGS = {
     "pide_batch_run": (_I, [_P, _I, _I, _P]),
     "pide_batch_destroy": (None, [_P]),
     "pide_reserve": (_I, [_P, _I]),
+    "pide_apply_noalloc": (_I, [_P, _P, _P, _I, _I, _P]),
     "pide_save": (_I, [_P, ctypes.c_char_p]),
     "pide_load": (_I, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "pide_get_handle_info": (_I, [_P, ctypes.POINTER(HandleInfo)]),
