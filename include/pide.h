@@ -273,6 +273,13 @@ pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);
  * kernel's mbarrier waits take. */
 pide_status pide_selftest_wait_timeout(int64_t budget_cycles, void* stream);
 
+/* Conversion self test: for n device inputs, writes the library's own
+ * integer-pipe conversions (binary64 -> bfloat16 round-to-nearest-even bits,
+ * binary32 -> binary64) beside CUDA's, so a test can compare them bit for bit. */
+pide_status pide_selftest_convert(const double* x_dev, const float* f_dev, int64_t n,
+                                  uint16_t* bf_mine, uint16_t* bf_cuda, double* d_mine,
+                                  double* d_cuda, void* stream);
+
 const char* pide_status_string(pide_status s);
 const char* pide_last_error(void);
 int32_t pide_version(void);

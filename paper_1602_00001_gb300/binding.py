@@ -73,6 +73,7 @@ _SIGS = {
     "pide_set_tuning": (_I, [_P, _I, _I]),
     "pide_get_tuning": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "pide_selftest_wait_timeout": (_I, [ctypes.c_int64, _P]),
+    "pide_selftest_convert": (_I, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "pide_status_string": (ctypes.c_char_p, [_I]),
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),

@@ -827,6 +827,34 @@ extern "C" pide_status pide_selftest_wait_timeout(int64_t budget_cycles, void* s
   return PIDE_OK;
 }
 
+// Bit-for-bit comparison of the integer-pipe conversions with CUDA's own.
+__global__ void convert_selftest_kernel(const double* __restrict__ x, const float* __restrict__ f,
+                                        long long n, uint16_t* __restrict__ bf_mine,
+                                        uint16_t* __restrict__ bf_cuda, double* __restrict__ d_mine,
+                                        double* __restrict__ d_cuda) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    bf_mine[i] = f64_to_bf16_bits(x[i]);
+    bf_cuda[i] = __bfloat16_as_ushort(__double2bfloat16(x[i]));
+    d_mine[i] = f32_to_f64(f[i]);
+    d_cuda[i] = (double)f[i];
+  }
+}
+
+extern "C" pide_status pide_selftest_convert(const double* x_dev, const float* f_dev, int64_t n,
+                                             uint16_t* bf_mine, uint16_t* bf_cuda,
+                                             double* d_mine, double* d_cuda, void* stream) {
+  if (n < 0 || (n > 0 && (!x_dev || !f_dev || !bf_mine || !bf_cuda || !d_mine || !d_cuda))) {
+    set_error("pide_selftest_convert: bad argument");
+    return PIDE_EINVAL;
+  }
+  if (n == 0) return PIDE_OK;
+  convert_selftest_kernel<<<256, 256, 0, (cudaStream_t)stream>>>(x_dev, f_dev, (long long)n,
+                                                                 bf_mine, bf_cuda, d_mine, d_cuda);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
 extern "C" const char* pide_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int32_t pide_version(void) { return 1; }

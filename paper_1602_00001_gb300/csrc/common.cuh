@@ -250,6 +250,41 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// ---- IEEE 754 conversions on the integer pipe.  GB300's FP64 pipe is
+// narrow (about 1 TFLOP/s); conversions issued there compete with the FP64
+// stencil and the FP64 accumulation of u.  These follow the binary formats'
+// definitions (sign | biased exponent | fraction) and hand the rare
+// special cases (zero handled here; subnormal, overflow, inf, NaN) to the
+// hardware conversion.
+
+// binary32 -> binary64, exact.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t x = __float_as_uint(f);
+  const uint32_t e = (x >> 23) & 0xFFu;
+  if ((x & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((uint64_t)x << 32));
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const uint64_t bits = ((uint64_t)(x & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                        ((uint64_t)(x & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// binary64 -> bfloat16 bits, round to nearest, ties to even.  bfloat16 keeps
+// 7 fraction bits with binary32's exponent range: the 45 dropped fraction
+// bits decide the rounding (above half: up; exactly half: to even).
+__device__ __forceinline__ uint16_t f64_to_bf16_bits(double v) {
+  const uint64_t u = (uint64_t)__double_as_longlong(v);
+  const uint32_t sign = (uint32_t)(u >> 48) & 0x8000u;
+  const int eb = (int)((u >> 52) & 0x7FF) - 896;   // rebias 1023 -> 127
+  if ((u << 1) == 0) return (uint16_t)sign;
+  if (eb <= 0 || eb >= 255) return __bfloat16_as_ushort(__double2bfloat16(v));
+  const uint64_t m = u & 0xFFFFFFFFFFFFFull;
+  uint32_t r = ((uint32_t)eb << 7) | (uint32_t)(m >> 45);
+  const uint64_t rest = m & 0x1FFFFFFFFFFFull;
+  const uint64_t half = 0x100000000000ull;
+  if (rest > half || (rest == half && (r & 1u))) r += 1u;
+  return (uint16_t)(sign | r);
+}
+
 // ---- tcgen05 (5th-generation tensor cores, accumulators in TMEM)
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {

@@ -276,7 +276,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       tc_fence_after();
       const int p = mt * BM + row_in_tile;
       const bool prow = p < n;
-      const double rs = (row_scale && prow) ? (double)row_scale[p] : 1.0;
+      const float rs = (FP8 && prow) ? row_scale[p] : 1.0f;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ++ch) {
@@ -289,8 +289,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           for (int j = 0; j < 32; ++j) {
             const int col = colbase + j;
             if (col < B) {
-              double val = (double)__uint_as_float(v[j]) * rs;
-              if (col_scale) val *= (double)col_scale[col];
+              // scales applied in FP32 (the FP8 apply is good to ~2^-8 anyway);
+              // one FP64 operation per element: the add into u
+              float a = __uint_as_float(v[j]);
+              if (FP8) a = a * rs * col_scale[col];
+              const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
               if (!whole) atomicAdd(dst, val);
               else *dst = accumulate ? *dst + val : val;

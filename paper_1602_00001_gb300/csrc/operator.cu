@@ -79,7 +79,7 @@ __device__ __forceinline__ void store_rhs(void* R, size_t idx, double v, float i
   } else if constexpr (RF == RF_F32) {
     reinterpret_cast<float*>(R)[idx] = (float)v;
   } else if constexpr (RF == RF_BF16) {
-    reinterpret_cast<__nv_bfloat16*>(R)[idx] = __double2bfloat16(v);
+    reinterpret_cast<uint16_t*>(R)[idx] = f64_to_bf16_bits(v);
   } else {
     reinterpret_cast<__nv_fp8_e4m3*>(R)[idx] = __nv_fp8_e4m3((float)(v * (double)inv_scale));
   }
