@@ -336,8 +336,7 @@ def main():
                      "avg_launch_ms": gemm_ms, "launches": apply_launches,
                      "algorithmic_flops_per_launch": flops_total / max(apply_launches, 1)},
         "kernel_ms_per_step": {c: prof[c][1] / args.steps for c in prof},
-        "overlap": "FP64 residual of one column group runs on a second stream under the "
-                   "other group's GEMM; per-kernel times can sum to more than ms_per_step",
+        "overlap": bool(s.get_tuning()["overlap"]),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * 8,
                 "d2h_bytes_per_step": B * n * 8},

@@ -251,17 +251,21 @@ pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
  *   PIDE_TUNE_GEMM_BN       tensor-core tile width for B > 128: 128 or 256 (default 256)
  *   PIDE_TUNE_GEMM_STREAMK  1: split the last partial wave of tiles over all SMs by
  *                           k-blocks (FP64 atomic partial sums); 0: whole tiles only
- *   PIDE_TUNE_OVERLAP       1 (default): for B >= 512 with tol <= 0, split the columns in
+ *   PIDE_TUNE_OVERLAP       1: for B >= 512 with tol <= 0, split the columns in
  *                           two groups and run each group's FP64 residual on a
  *                           low-priority internal stream under the other group's
- *                           tensor-core apply; 0: one stream, whole batch per phase */
+ *                           tensor-core apply; 0 (default): one stream, whole batch per
+ *                           phase (measured faster on GB300: the two overlapped kernels
+ *                           slow each other by more than the residual's time)
+ *   PIDE_TUNE_RESID_CTAS    residual CTAs (256 threads) per SM while overlapped: 1..8 (default 2) */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
   PIDE_TUNE_GEMV_MAX_B = 2,
   PIDE_TUNE_GEMM_BN = 3,
   PIDE_TUNE_GEMM_STREAMK = 4,
-  PIDE_TUNE_OVERLAP = 5
+  PIDE_TUNE_OVERLAP = 5,
+  PIDE_TUNE_RESID_CTAS = 6
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -177,8 +177,7 @@ static pide_status solve_overlapped(pide_ctx* c, const double* b, int mode, cons
       PIDE_CUDA_TRY(cudaStreamWaitEvent(c->aux, appl[g], 0));
       if (rf == RF_E4M3)
         PIDE_TRY(launch_fp8_scales(c, b, x, gn[g], mode, lift, true, c->aux, g0[g]));
-      PIDE_TRY(launch_residual(c, b, x, gn[g], mode, lift, rf, true, nullptr, false, true, c->aux,
-                               g0[g]));
+      PIDE_TRY(launch_residual_persistent(c, b, x, gn[g], mode, lift, rf, c->aux, g0[g]));
       PIDE_CUDA_TRY(cudaEventRecord(c->ev[4 + g], c->aux));
     }
   }
@@ -756,6 +755,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 0 && value != 1) break;
       h->overlap = value;
       return PIDE_OK;
+    case PIDE_TUNE_RESID_CTAS:
+      if (value < 1 || value > 8) break;
+      h->resid_ctas_per_sm = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -773,6 +776,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_GEMM_BN: *value = h->gemm_bn_large; return PIDE_OK;
     case PIDE_TUNE_GEMM_STREAMK: *value = h->gemm_streamk; return PIDE_OK;
     case PIDE_TUNE_OVERLAP: *value = h->overlap; return PIDE_OK;
+    case PIDE_TUNE_RESID_CTAS: *value = h->resid_ctas_per_sm; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

@@ -85,7 +85,8 @@ struct pide_ctx {
   // launch-shape knobs (pide_set_tuning; the autotuner sets them)
   int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
   int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
-  int overlap = 1;                  // residual of one column group under the GEMM of the other
+  int overlap = 0;                  // residual of one column group under the GEMM of the other
+  int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
   cudaStream_t aux = nullptr;       // low-priority stream for the overlapped residuals
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
@@ -118,6 +119,11 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
                             bool honor_done, cudaStream_t st, int col0 = 0);
 pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
+// Residual with a small persistent grid (num_sms * resid_ctas_per_sm blocks), for the
+// overlapped schedule; writes R only.
+pide_status launch_residual_persistent(pide_ctx* c, const double* b, const double* u, int B,
+                                      int mode, const double* lift, int rfmt, cudaStream_t st,
+                                      int col0);
 // FP8 right-hand sides: per-column scale max|f~|/448 (prep) or max|r~|/448 (residual).
 pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int B, int mode,
                               const double* lift, bool from_residual, cudaStream_t st,

@@ -79,7 +79,7 @@ __device__ __forceinline__ void store_rhs(void* R, size_t idx, double v, float i
   } else if constexpr (RF == RF_F32) {
     reinterpret_cast<float*>(R)[idx] = (float)v;
   } else if constexpr (RF == RF_BF16) {
-    reinterpret_cast<uint16_t*>(R)[idx] = f64_to_bf16_bits(v);
+    reinterpret_cast<__nv_bfloat16*>(R)[idx] = __double2bfloat16(v);
   } else {
     reinterpret_cast<__nv_fp8_e4m3*>(R)[idx] = __nv_fp8_e4m3((float)(v * (double)inv_scale));
   }
@@ -165,6 +165,42 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
   if (track) {
     mxr = block_max(mxr, red);
     if (threadIdx.x == 0) atomic_max_nonneg(&colmax_r[col], mxr);
+  }
+}
+
+// The same residual over a flat index (column * n + p) with a small persistent
+// grid: used under a concurrently running tensor-core apply, where a full-size
+// grid would crowd the SMs' warp schedulers that the GEMM's single-thread TMA
+// and MMA issuers depend on.
+template <int RF>
+__global__ void residual_flat_kernel(const double* __restrict__ b, const double* __restrict__ u,
+                                     int n, int mx, int B, int ldr, int mode,
+                                     const double* __restrict__ w4,
+                                     const double* __restrict__ dinv,
+                                     const double* __restrict__ lift, void* __restrict__ R,
+                                     const float* __restrict__ col_scale,
+                                     const uint32_t* __restrict__ flags) {
+  if (flags && flags[FLAG_DONE]) return;
+  const long long total = (long long)B * n;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int col = (int)(k / n);
+    const int p = (int)(k - (long long)col * n);
+    const int c = p % mx;
+    const double* uc = u + (size_t)col * n;
+    // streaming loads (evict-first): keep the concurrent GEMM's operands in L2
+    const double bp = __ldcs(b + k);
+    const double up = __ldcs(uc + p);
+    double r;
+    if (mode == 1) r = fma(bp, dinv[p], -up);
+    else if (lift) r = bp + (lift[p] - up);
+    else r = bp - up;
+    if (c > 0) r = fma(w4[p], __ldcs(uc + p - 1), r);
+    if (c < mx - 1) r = fma(w4[n + p], __ldcs(uc + p + 1), r);
+    if (p >= mx) r = fma(w4[2 * n + p], __ldcs(uc + p - mx), r);
+    if (p + mx < n) r = fma(w4[3 * n + p], __ldcs(uc + p + mx), r);
+    const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
+    store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
   }
 }
 
@@ -327,6 +363,27 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
     case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
+  }
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_residual_persistent(pide_ctx* c, const double* b, const double* u, int B,
+                                      int mode, const double* lift, int rfmt, cudaStream_t st,
+                                      int col0) {
+  if (B == 0) return PIDE_OK;
+  ProfScope ps(c, st, 1);
+  const size_t off = (size_t)col0 * c->n;
+  b += off;
+  u += off;
+  void* R = (uint8_t*)c->R + (size_t)col0 * c->ld * rhs_elem_bytes(rfmt);
+  const int grid = c->num_sms * c->resid_ctas_per_sm;
+  const float* cs = c->col_scale + col0;
+  switch (rfmt) {
+    case RF_F32: residual_flat_kernel<RF_F32><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_BF16: residual_flat_kernel<RF_BF16><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_E4M3: residual_flat_kernel<RF_E4M3><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, cs, c->flags); break;
+    default: residual_flat_kernel<RF_F64><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
