@@ -125,14 +125,18 @@ pide_status ensure_workspace(pide_ctx* c, int B) {
   if (c->R) cudaFree(c->R);
   if (c->col_scale) cudaFree(c->col_scale);
   if (c->colmax) cudaFree(c->colmax);
+  if (c->Rf) cudaFree(c->Rf);
   c->R = nullptr;
   c->col_scale = nullptr;
   c->colmax = nullptr;
+  c->Rf = nullptr;
   c->ws_B = 0;
   const size_t esz = c->prec == PIDE_FP64 ? 8 : 4;
   PIDE_CUDA_TRY(cudaMalloc(&c->R, (size_t)nb * c->ld * esz));
   PIDE_CUDA_TRY(cudaMemset(c->R, 0, (size_t)nb * c->ld * esz));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->col_scale, (size_t)nb * sizeof(float)));
+  if (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2)
+    PIDE_CUDA_TRY(cudaMalloc((void**)&c->Rf, (size_t)nb * c->ld * sizeof(float)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->colmax, 3 * (size_t)nb * sizeof(double)));
   PIDE_CUDA_TRY(cudaMemset(c->colmax, 0, 3 * (size_t)nb * sizeof(double)));
   c->ws_B = nb;
@@ -203,6 +207,11 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
   PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
   for (int k = 0; k < sweeps; ++k) {
+    if (rf == RF_E4M3 && tol <= 0) {
+      PIDE_TRY(launch_residual_fp8(c, b, x, B, mode, lift, st));
+      PIDE_TRY(launch_apply(c, B, x, true, st));
+      continue;
+    }
     if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, x, B, mode, lift, true, st));
     PIDE_TRY(launch_residual(c, b, x, B, mode, lift, rf, true, nullptr, tol > 0, true, st));
     if (tol > 0) PIDE_TRY(launch_check(c, B, tol, st));
@@ -394,7 +403,7 @@ extern "C" void pide_destroy(pide_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {h->eps, h->cf, h->d, h->dinv, h->w, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
+  void* ptrs[] = {h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
                   h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u};
   for (void* p : ptrs)
     if (p) cudaFree(p);

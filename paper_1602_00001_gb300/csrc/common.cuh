@@ -73,6 +73,7 @@ struct pide_ctx {
   int ws_B = 0;
   void* R = nullptr;                // [ws_B][ld] quantised right-hand side / residual
   float* col_scale = nullptr;       // [ws_B] per-column scale (FP8 formats)
+  float* Rf = nullptr;              // [ws_B][ld] FP32 residual before FP8 quantisation
   double* lift = nullptr;           // [n] boundary lifting sum_q w_pq g_q
   double* colmax = nullptr;         // [3][ws_B] column maxima: |r|, |b|, raw (FP8 scales)
   uint32_t* flags = nullptr;        // FLAG_COUNT words
@@ -119,6 +120,10 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
                             bool honor_done, cudaStream_t st, int col0 = 0);
 pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
+// FP8 right-hand sides in one FP64 pass: residual to FP32 scratch with the column
+// maxima, per-column scale, then e4m3 quantisation of the scratch into R.
+pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, int B, int mode,
+                                const double* lift, cudaStream_t st);
 // Residual with a small persistent grid (num_sms * resid_ctas_per_sm blocks), for the
 // overlapped schedule; writes R only.
 pide_status launch_residual_persistent(pide_ctx* c, const double* b, const double* u, int B,

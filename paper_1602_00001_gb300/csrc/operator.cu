@@ -457,6 +457,38 @@ __global__ void finalize_scale_kernel(double* __restrict__ colmax_raw, float* __
 
 }  // namespace
 
+namespace {
+__global__ void finalize_scale_kernel(double* __restrict__ colmax_raw, float* __restrict__ col_scale,
+                                      int B, const uint32_t* __restrict__ flags);
+__global__ void quantize_e4m3_kernel(const float* __restrict__ Rf, int n, int ld,
+                                     const float* __restrict__ col_scale,
+                                     __nv_fp8_e4m3* __restrict__ R,
+                                     const uint32_t* __restrict__ flags) {
+  if (flags[FLAG_DONE]) return;
+  const int col = blockIdx.y;
+  const float isc = 1.0f / col_scale[col];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    R[(size_t)col * ld + p] = __nv_fp8_e4m3((float)((double)Rf[(size_t)col * ld + p] * (double)isc));
+}
+}  // namespace
+
+pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, int B, int mode,
+                                const double* lift, cudaStream_t st) {
+  if (B == 0) return PIDE_OK;
+  ProfScope ps(c, st, 1);
+  dim3 g = col_grid(c->n, B);
+  double* raw = c->colmax + 2 * (size_t)c->ws_B;
+  residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift,
+                                             c->Rf, nullptr, nullptr, raw, 1, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  finalize_scale_kernel<<<(B + 255) / 256, 256, 0, st>>>(raw, c->col_scale, B, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  quantize_e4m3_kernel<<<g, 256, 0, st>>>(c->Rf, c->n, c->ld, c->col_scale,
+                                          (__nv_fp8_e4m3*)c->R, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
 pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int B, int mode,
                               const double* lift, bool from_residual, cudaStream_t st, int col0) {
   if (B == 0) return PIDE_OK;
