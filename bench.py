@@ -304,8 +304,17 @@ def main():
     value = whole_job_rate(world, B, args.steps, ms_total)
     err_final = err_of(u)
 
-    # B = 1 rate
+    pk, pk_kind = peaks()
+    # B = 1 rate, and the HBM roofline of its apply kernel (live CUDA events)
     b1_ms = timed(lambda: s.apply(b1, u1, sweeps=k1), 10)
+    with s.profile() as prof1:
+        for _ in range(5):
+            s.apply(b1, u1, sweeps=k1)
+    b1_apply_launches, b1_apply_ms = prof1["apply"]
+    hi = s.info()
+    b1_bytes = hi.store_bytes if not (args.precision == "bf16" and s.get_tuning()["symv"]) else \
+        2 * 2 * (((n + 127) // 128) * (((n + 127) // 128) + 1) // 2) * 128 * 128
+    b1_gbs = b1_bytes * b1_apply_launches / (b1_apply_ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     b_host = b.cpu().pin_memory()
@@ -321,7 +330,6 @@ def main():
     e2e_value = world * B / e2e_s
 
     # ---- roofline of the dominant kernel (the apply GEMM), from live CUDA events
-    pk, pk_kind = peaks()
     apply_launches, apply_ms = prof["apply"]
     gemm_ms = apply_ms / max(apply_launches, 1)
     # every timed step applies the stored inverse (1 + k) times to all B columns
@@ -354,7 +362,11 @@ def main():
         "accuracy": {"max_rel_err_eq6_vs_fp64": err_final, "target": 1e-6,
                      "sampled_columns": len(sample_cols),
                      "err_by_sweeps": {str(kk): v for kk, v in calib.items()}},
-        "b1": {"value": 1.0 / (b1_ms * 1e-3), "unit": UNIT, "sweeps": k1, "ms": b1_ms},
+        "b1": {"value": 1.0 / (b1_ms * 1e-3), "unit": UNIT, "sweeps": k1, "ms": b1_ms,
+               "path": "symmetric S^-1, BF16 hi+lo packed lower tiles" if (args.precision == "bf16" and s.get_tuning()["symv"]) else "GEMV over the stored L^-1",
+               "roofline": {"bound": "hbm", "achieved": b1_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                            "frac": b1_gbs / pk["hbm_gbs"], "bytes_per_apply": b1_bytes,
+                            "avg_apply_ms": b1_apply_ms / max(b1_apply_launches, 1)}},
         "fp64_gpu": {"b1_solves_per_s": 1.0 / (fp64_b1_ms * 1e-3),
                      "b64_solves_per_s": 64.0 / (fp64_b64_ms * 1e-3),
                      "speedup_b1024_vs_fp64": value / world / (64.0 / (fp64_b64_ms * 1e-3)),

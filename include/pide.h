@@ -102,7 +102,10 @@ typedef struct {
  *             finite and > 0 (NULL means eps = 1, the case of Eq. 2).
  *   p         storage format of the inverse.  The inverse is always formed
  *             in FP64 on the GPU (block-tridiagonal elimination), then
- *             quantised; the FP64 copy is kept only for PIDE_FP64.
+ *             quantised; the FP64 copy is kept only for PIDE_FP64.  BF16
+ *             handles also keep the lower triangle of the symmetric S^-1 in
+ *             128 x 128 tiles of two BF16 terms (hi + lo, the size of the
+ *             one-term L^-1) for one-column applies.
  *   stream    cudaStream_t for all setup work (the call synchronises it).
  *   out       receives the new handle (NULL on failure).
  * Errors: EINVAL (bad grid, eps), ENOMEM, ECUDA, EUNSUPPORTED (not sm_103).
@@ -257,7 +260,12 @@ pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
  *                           tensor-core apply; 0 (default): one stream, whole batch per
  *                           phase (measured faster on GB300: the two overlapped kernels
  *                           slow each other by more than the residual's time)
- *   PIDE_TUNE_RESID_CTAS    residual CTAs (256 threads) per SM while overlapped: 1..8 (default 2) */
+ *   PIDE_TUNE_RESID_CTAS    residual CTAs (256 threads) per SM while overlapped: 1..8 (default 2)
+ *   PIDE_TUNE_SYMV          1 (default): BF16 handles apply B = 1 through the packed lower
+ *                           triangle of the symmetric S^-1 (L^-1 = S^-1 D) in two BF16 terms,
+ *                           ~16 significant bits for the bytes of the one-term L^-1, so
+ *                           refinement needs about a quarter of the sweeps;
+ *                           0: through the one-term L^-1 (GEMV) */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -265,7 +273,8 @@ typedef enum {
   PIDE_TUNE_GEMM_BN = 3,
   PIDE_TUNE_GEMM_STREAMK = 4,
   PIDE_TUNE_OVERLAP = 5,
-  PIDE_TUNE_RESID_CTAS = 6
+  PIDE_TUNE_RESID_CTAS = 6,
+  PIDE_TUNE_SYMV = 7
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -239,7 +239,7 @@ class Solver:
         return db, deps
 
     TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3,
-                 "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6}
+                 "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6, "symv": 7}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

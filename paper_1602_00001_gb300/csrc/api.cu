@@ -149,6 +149,7 @@ pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStr
                          int col0) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 0);
+  if (col0 == 0 && B == 1 && c->sym && c->symv) return launch_symv(c, u, accumulate, st);
   if (col0 == 0 && B <= c->gemv_max_b) return launch_gemv(c, B, u, accumulate, st);
   if (col0 == 0 && (c->prec == PIDE_FP64 || c->prec == PIDE_FP32))
     return launch_gemm_simt(c, B, u, accumulate, st);
@@ -320,6 +321,7 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->w, 4 * (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->lift, (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->flags, FLAG_COUNT * sizeof(uint32_t)));
+
   PIDE_CUDA_TRY(cudaMemset(c->flags, 0, FLAG_COUNT * sizeof(uint32_t)));
   int prio_lo = 0, prio_hi = 0;
   PIDE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
@@ -378,6 +380,7 @@ extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pi
       G = nullptr;
     } else {
       s = quantize_store(c, G, st);
+      if (s == PIDE_OK && p == PIDE_BF16) s = build_sym_store(c, G, st);
     }
   }
   if (s == PIDE_OK) s = make_tma_maps(c);
@@ -403,7 +406,7 @@ extern "C" void pide_destroy(pide_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
+  void* ptrs[] = {h->sym, h->sym_lo, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
                   h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -768,6 +771,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value < 1 || value > 8) break;
       h->resid_ctas_per_sm = value;
       return PIDE_OK;
+    case PIDE_TUNE_SYMV:
+      if (value != 0 && value != 1) break;
+      h->symv = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -786,6 +793,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_GEMM_STREAMK: *value = h->gemm_streamk; return PIDE_OK;
     case PIDE_TUNE_OVERLAP: *value = h->overlap; return PIDE_OK;
     case PIDE_TUNE_RESID_CTAS: *value = h->resid_ctas_per_sm; return PIDE_OK;
+    case PIDE_TUNE_SYMV: *value = h->symv; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

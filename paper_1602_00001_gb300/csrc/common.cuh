@@ -67,6 +67,12 @@ struct pide_ctx {
   void* inv_lo = nullptr;           // [n][ld] e4m3 lo term (FP8X2)
   float* row_scale = nullptr;       // [n] per-row scale (FP8 formats)
   size_t store_bytes = 0;
+  void* sym = nullptr;              // packed lower 128x128 BF16 tiles of S^-1, hi term (B = 1 apply)
+  void* sym_lo = nullptr;           // same layout, lo term bf16(S^-1 - hi)
+  long long sym_tiles = 0;
+  size_t sym_bytes = 0;
+  float* dfl = nullptr;             // [n] d as float (x = D r formed on the fly)
+  float* ysum = nullptr;            // [n] FP32 accumulation of the symmetric apply
   bool tmA_ok = false;
   CUtensorMap tmA, tmA_lo;          // TMA maps over the stored inverse (tensor-core formats)
   // workspace (grown on demand; pide_reserve pre-sizes it)
@@ -93,6 +99,7 @@ struct pide_ctx {
   int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
   int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8
+  int symv = 1;                     // B = 1 through the packed symmetric S^-1 (half the bytes)
   // profiling
   bool prof_on = false;
   struct Ev { cudaEvent_t a, b; int cls; };
@@ -145,6 +152,8 @@ int rhs_format(const pide_ctx* c, int B);   // element format R must hold for th
 pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
                            int col0 = 0);
 pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
+pide_status build_sym_store(pide_ctx* c, const double* G, cudaStream_t st);   // G = L^-1 (FP64)
+pide_status launch_symv(pide_ctx* c, double* u, bool accumulate, cudaStream_t st);
 pide_status launch_gemm_simt(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 
 pide_status launch_face_grad(pide_ctx* c, const double* mu, const double* u, const double* b,

@@ -128,6 +128,7 @@ def test_bf16_single_apply_is_exact_contraction(B):
     eps = W.eps_fourier(nx, ny, h, seed=11)
     b = _b(nx, ny, h, eps, B, seed=B)
     s = _solver(nx, ny, h, eps, "bf16")
+    s.set_tuning(symv=0)          # B = 1 through the full stored L^-1 here
     for limit in ([1, 8] if B <= 8 else [1]):
         s.set_tuning(gemv_max_b=limit)
         u = s.apply(b, sweeps=0).cpu().numpy()
@@ -326,3 +327,44 @@ def test_overlapped_refinement(B):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(u, u_eager)
+
+
+@pytest.mark.parametrize("nx,ny", [(40, 33), (131, 12), (12, 140), (3, 3)])
+def test_symv_single_apply_is_exact_contraction(nx, ny):
+    """B = 1 through the packed lower triangle of S^-1 = L^-1 D^-1 (BF16 hi +
+    BF16 lo, 128 x 128 tiles; upper blocks are the transposes of the stored
+    lower ones) with x = D r formed in FP32: equals the FP64 contraction of the
+    same rounded operands up to FP32 accumulation."""
+    h = 1.0 / (max(nx, ny) - 1)
+    eps = W.eps_lognormal(nx, ny, seed=nx + ny)
+    b = _b(nx, ny, h, eps, 1, seed=5)
+    s = _solver(nx, ny, h, eps, "bf16")
+    u = s.apply(b, sweeps=0).cpu().numpy()
+    Linv = O.interior_inverse(nx, ny, eps)
+    d = O.diagonal_d(nx, ny, eps)
+    S = Linv / d[None, :]
+    hi = O.round_bf16(S)
+    Sl = hi + O.round_bf16(S - hi)
+    blk = np.arange(s.n) // 128
+    lower = blk[:, None] >= blk[None, :]
+    A = np.where(lower, Sl, Sl.T)
+    x = O.round_fp32(O.round_fp32(b[0]) * O.round_fp32(d))
+    ref = A @ x
+    mag = np.abs(A) @ np.abs(x)
+    err = np.abs(u[0] - ref)
+    assert np.all(err <= 2e-5 * mag + 1e-300), float(np.max(err / mag))
+    # two terms: far closer to the exact inverse than one BF16 term
+    assert O.rel_error_eq6(u, (Linv @ b[0])[None, :]) < 5e-5
+
+
+def test_symv_refined_matches_gemv():
+    nx = ny = 60
+    h = 1.0 / 59
+    eps = W.eps_fourier(nx, ny, h, seed=8)
+    b = _b(nx, ny, h, eps, 1, seed=9)
+    ref = O.solve(nx, ny, eps, b, route="band")
+    s = _solver(nx, ny, h, eps, "bf16")
+    for symv in (1, 0):
+        s.set_tuning(symv=symv)
+        u = s.apply(b, sweeps=6).cpu().numpy()
+        assert O.rel_error_eq6(u, ref) < 1e-6, symv
