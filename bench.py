@@ -177,6 +177,114 @@ def reference_arm(args):
     return 0
 
 
+def _evt_time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    z.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(z) / reps
+
+
+def batched_workload(args):
+    """64 independent grids (side uniform over {32,48,64,96,128}, lognormal eps
+    sigma 0.5), ragged B_k uniform over 1..64, FP32 and BF16 stores alternating:
+    one plan (one launch per phase, replayed from a CUDA graph) against a loop
+    of per-problem pide_apply calls with the same sweep count."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import pide_oracle as O
+    from paper_1602_00001_gb300 import workloads as W
+    from paper_1602_00001_gb300.binding import Solver, BatchPlan
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    probs = W.batched_problem_set(seed=3, nprob=64)
+    solvers, bs, us = [], [], []
+    for k, (side, eps, rho) in enumerate(probs):
+        h = 1.0 / (side - 1)
+        sv = Solver(side, side, h, eps, "fp32" if k % 2 == 0 else "bf16")
+        bd = sv.rhs_from_charge(torch.from_numpy(rho).cuda())
+        solvers.append(sv)
+        bs.append(bd)
+        us.append(torch.empty_like(bd))
+    total_rhs = sum(b.shape[0] for b in bs)
+    sweeps = args.sweeps if args.sweeps >= 0 else 6
+    plan = BatchPlan(solvers, bs, us)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        plan.run(sweeps, use_graph=True, stream=st)
+    st.synchronize()
+    errs = []
+    for k in (0, 1, 2, 3):
+        side, eps, rho = probs[k]
+        b_np = bs[k].cpu().numpy()
+        errs.append(O.rel_error_eq6(us[k].cpu().numpy(), O.solve(side, side, eps, b_np)))
+    with torch.cuda.stream(st):
+        ms_batched = _evt_time(lambda: plan.run(sweeps, use_graph=True, stream=st), args.steps)
+
+    def loop():
+        for sv, b, u in zip(solvers, bs, us):
+            sv.apply(b, u, sweeps=sweeps)
+    ms_loop = _evt_time(loop, max(3, args.steps // 4))
+    launches = 2 + 2 * sweeps
+    line = {"metric": "RHS solves/s, 64 uneven grids (batched)", "value": total_rhs / (ms_batched * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": ms_batched,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "64 grids, side in {32,48,64,96,128}, lognormal eps, B_k in 1..64",
+                       "total_rhs": total_rhs, "sweeps": sweeps,
+                       "sizes": [int(p[0]) for p in probs]},
+            "per_problem_loop": {"ms_per_step": ms_loop, "value": total_rhs / (ms_loop * 1e-3)},
+            "speedup_vs_loop": ms_loop / ms_batched, "gpu_launches_per_step": launches,
+            "accuracy": {"max_rel_err_eq6_vs_oracle_4_problems": max(errs)}}
+    print(json.dumps(line))
+    return 0
+
+
+def adjoint_workload(args):
+    """128 x 128 nodes (126^2 unknowns), lognormal eps, B = 32: forward refined
+    apply plus the backward (adjoint solve, dLoss/db, dLoss/deps) per step."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import pide_oracle as O
+    from paper_1602_00001_gb300 import workloads as W
+    from paper_1602_00001_gb300.binding import Solver
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    N, B = 128, 32
+    h = 1.0 / (N - 1)
+    eps = W.eps_lognormal(N, N, seed=4)
+    s = Solver(N, N, h, eps, "bf16")
+    b = s.rhs_from_charge(torch.from_numpy(W.gaussian_blobs(N, N, h, seed=40, batch=B)).cuda())
+    ut = s.apply(s.rhs_from_charge(torch.from_numpy(W.gaussian_blobs(N, N, h, seed=41, batch=B)).cuda()), sweeps=6)
+    sweeps = args.sweeps if args.sweeps >= 0 else 5
+
+    def step():
+        u = s.apply(b, sweeps=sweeps)
+        return s.backward(u - ut, u, b, sweeps=sweeps)
+    db, deps = step()
+    b_np = b.cpu().numpy()
+    u_o = O.solve(N, N, eps, b_np, route="band")
+    _, db_o, deps_o = O.adjoint_gradients(N, N, eps, b_np, u_o - ut.cpu().numpy())
+    err_db = float(np.max(np.abs(db.cpu().numpy() - db_o)) / np.max(np.abs(db_o)))
+    err_de = float(np.max(np.abs(deps.cpu().numpy() - deps_o)) / np.max(np.abs(deps_o)))
+    ms = _evt_time(step, args.steps)
+    line = {"metric": "forward+backward RHS/s, 126^2 grid, B=32", "value": B / (ms * 1e-3),
+            "unit": "RHS/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic", "config": {"workload": "128x128 nodes, lognormal eps, B=32",
+                                            "sweeps": sweeps},
+            "accuracy": {"db_rel_err_vs_oracle": err_db, "deps_rel_err_vs_oracle": err_de}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,9 +296,15 @@ def main():
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--nodes", type=int, default=NODES, help="grid nodes per side (profiling runs)")
+    ap.add_argument("--workload", default="apply", choices=["apply", "batched", "adjoint"],
+                    help="apply: the headline (default); batched / adjoint: the other rows")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batched":
+        return batched_workload(args)
+    if args.workload == "adjoint":
+        return adjoint_workload(args)
 
     import numpy as np
     import torch
