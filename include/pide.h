@@ -192,7 +192,9 @@ pide_status pide_apply_backward(pide_handle h, const double* gout_dev, const dou
  *
  * pide_batch_create  builds the plan (allocates; synchronous).  Handles must
  *                    outlive the plan and share one device; b/u pointers are
- *                    fixed in the plan.  EUNSUPPORTED for FP64/FP8 stores.
+ *                    fixed in the plan.  sweeps_k (may be NULL): per-problem
+ *                    cap on the refinement sweeps (a problem skips the phases
+ *                    past its cap).  EUNSUPPORTED for FP64/FP8 stores.
  * pide_batch_run     enqueues one refined batched apply with `sweeps` sweeps.
  *                    use_graph != 0 (and a non-NULL stream): the launches are
  *                    captured into a CUDA graph on the first run with a given
@@ -201,7 +203,8 @@ pide_status pide_apply_backward(pide_handle h, const double* gout_dev, const dou
  * pide_apply_batched create + run + synchronise + destroy in one call.
  */
 pide_status pide_batch_create(const pide_handle* hs, int32_t nprob, const double* const* b,
-                              double* const* u, const int32_t* Bs, pide_batch_handle* out);
+                              double* const* u, const int32_t* Bs, const int32_t* sweeps_k,
+                              pide_batch_handle* out);
 pide_status pide_batch_run(pide_batch_handle p, int32_t sweeps, int32_t use_graph, void* stream);
 void pide_batch_destroy(pide_batch_handle p);
 pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob, const double* const* b,

@@ -59,7 +59,7 @@ _SIGS = {
     "pide_rhs_from_charge": (_I, [_P, _P, _P, _I, _P]),
     "pide_apply_backward": (_I, [_P, _P, _P, _P, _P, _P, _I, _I, _P]),
     "pide_apply_batched": (_I, [_P, _I, _P, _P, _P, _I, _P]),
-    "pide_batch_create": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_P)]),
+    "pide_batch_create": (_I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "pide_batch_run": (_I, [_P, _I, _I, _P]),
     "pide_batch_destroy": (None, [_P]),
     "pide_reserve": (_I, [_P, _I]),
@@ -314,16 +314,20 @@ class BatchPlan:
     """pide_batch_create / run / destroy: the uneven-grid batched apply with
     optional CUDA-graph replay (buffers are fixed in the plan)."""
 
-    def __init__(self, solvers, bs, us):
+    def __init__(self, solvers, bs, us, sweeps_per_problem=None):
         self.lib = load_library()
         k = len(solvers)
         self._keep = (solvers, bs, us)
+        sk = None
+        if sweeps_per_problem is not None:
+            sk = (ctypes.c_int32 * k)(*[int(x) for x in sweeps_per_problem])
         hs = (ctypes.c_void_p * k)(*[s.handle.value for s in solvers])
         bp = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
         up = (ctypes.c_void_p * k)(*[u.data_ptr() for u in us])
         Bs = (ctypes.c_int32 * k)(*[b.reshape(-1, s.n).shape[0] for b, s in zip(bs, solvers)])
         out = ctypes.c_void_p()
-        _check(self.lib.pide_batch_create(hs, k, bp, up, Bs, ctypes.byref(out)), "pide_batch_create")
+        _check(self.lib.pide_batch_create(hs, k, bp, up, Bs, sk, ctypes.byref(out)),
+               "pide_batch_create")
         self.plan = out
 
     def run(self, sweeps: int = 2, use_graph: bool = True, stream=None):

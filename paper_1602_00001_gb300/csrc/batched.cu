@@ -3,16 +3,18 @@
 //
 // A plan (pide_batch_create) uploads a problem table and two device work
 // lists once:
-//   tile items  (problem, 64-row tile, 64-column tile), ordered largest work
+//   tile items  (problem, 128-row tile, 64-column tile), ordered largest work
 //               first (n_k x columns), pulled by persistent CTAs from an
 //               atomic counter -- the apply of every problem in ONE launch;
 //   column items (problem, column) -- prep and FP64 residual of every problem
 //               in one launch each.
 // pide_batch_run then issues prep, apply, and `sweeps` x (residual, apply):
 // 2 + 2*sweeps launches for the whole set, optionally replayed from a CUDA
-// graph captured on the first run.  The apply is a register-tiled FP32 SIMT
-// contraction (4 x 4 results per thread, columns contiguous per thread so
-// warps past a problem's last column skip their arithmetic).
+// graph captured on the first run.  Each problem may cap its own sweep count
+// (an FP32 store needs fewer than a BF16 one): its items are skipped in the
+// phases past its cap.  The apply is a register-tiled FP32 SIMT contraction
+// (8 x 4 results per thread, columns contiguous per thread so warps past a
+// problem's last column skip their arithmetic).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -29,10 +31,11 @@ struct BatchProb {
   double* u;            // [B][n]
   float* R;             // [B][ld] FP32 right-hand side / residual
   int ld, n, mx, B, fmt;  // fmt: 0 FP32, 1 BF16
-  int pad;
+  int pad;                // sweeps this problem runs (phases past it are skipped)
 };
 
-constexpr int BT = 64;   // rows and columns per tile item
+constexpr int BM = 128;  // rows per tile item
+constexpr int BT = 64;   // columns per tile item
 constexpr int BK = 32;   // K step
 
 __device__ __forceinline__ float load_a(const BatchProb& P, size_t idx) {
@@ -40,12 +43,15 @@ __device__ __forceinline__ float load_a(const BatchProb& P, size_t idx) {
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(P.inv)[idx]);
 }
 
+// 128 x 64 output tile per item, 256 threads: thread (tx, ty) owns rows
+// 4 tx .. +3 and 64 + 4 tx .. +3 and columns 4 ty .. +3 (32 accumulators);
+// per k it reads three float4 from shared memory for 32 FMAs.
 __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __restrict__ probs,
                                                             const int4* __restrict__ items,
                                                             int nitems, int* __restrict__ counter,
-                                                            int accumulate) {
-  __shared__ float As[BK][BT + 4];
-  __shared__ float Xs[BK][BT + 4];
+                                                            int accumulate, int phase) {
+  __shared__ __align__(16) float As[BK][BM + 4];
+  __shared__ __align__(16) float Xs[BK][BT + 4];
   __shared__ int s_item;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   while (true) {
@@ -56,37 +62,43 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
     if (it >= nitems) break;
     const int4 w = items[it];
     const BatchProb P = probs[w.x];
-    const int p0 = w.y * BT, c0 = w.z * BT;
+    if (phase > P.pad) continue;                      // this problem already ran its sweeps
+    const int p0 = w.y * BM, c0 = w.z * BT;
     const int ncols = min(BT, P.B - c0);
     const bool active = ty * 4 < ncols;
-    float acc[4][4];
+    float acc[8][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (int k0 = 0; k0 < P.n; k0 += BK) {
+#pragma unroll
+      for (int q = 0; q < (BM * BK) / 256; ++q) {
+        const int e = threadIdx.x + 256 * q;
+        const int r = e / BK, kk = e % BK;
+        const int gk = k0 + kk, gp = p0 + r;
+        As[kk][r] = (gp < P.n && gk < P.n) ? load_a(P, (size_t)gp * P.ld + gk) : 0.f;
+      }
 #pragma unroll
       for (int q = 0; q < (BT * BK) / 256; ++q) {
         const int e = threadIdx.x + 256 * q;
         const int r = e / BK, kk = e % BK;
         const int gk = k0 + kk;
-        const int gp = p0 + r, gc = c0 + r;
-        As[kk][r] = (gp < P.n && gk < P.n) ? load_a(P, (size_t)gp * P.ld + gk) : 0.f;
-        Xs[kk][r] = (r < ncols && gk < P.n) ? P.R[(size_t)gc * P.ld + gk] : 0.f;
+        Xs[kk][r] = (r < ncols && gk < P.n) ? P.R[(size_t)(c0 + r) * P.ld + gk] : 0.f;
       }
       __syncthreads();
       if (active) {
-#pragma unroll 8
+#pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
-          float av[4], xv[4];
+          const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][4 * tx]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + 4 * tx]);
+          const float4 xv = *reinterpret_cast<const float4*>(&Xs[kk][4 * ty]);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+          for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) xv[j] = Xs[kk][ty * 4 + j];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xs[j], acc[i][j]);
         }
       }
       __syncthreads();
@@ -97,8 +109,8 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
         const int c = ty * 4 + j;
         if (c >= ncols) continue;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int p = p0 + tx + 16 * i;
+        for (int i = 0; i < 8; ++i) {
+          const int p = p0 + (i < 4 ? 4 * tx + i : 64 + 4 * tx + (i - 4));
           if (p >= P.n) continue;
           double* dst = P.u + (size_t)(c0 + c) * P.n + p;
           *dst = accumulate ? *dst + (double)acc[i][j] : (double)acc[i][j];
@@ -111,9 +123,10 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
 // Prep (residual == 0): R = float(b).  Residual: R = float(b - L u), FP64.
 __global__ void __launch_bounds__(256) batched_vec_kernel(const BatchProb* __restrict__ probs,
                                                           const int2* __restrict__ items,
-                                                          int residual) {
+                                                          int residual, int phase) {
   const int2 w = items[blockIdx.x];
   const BatchProb P = probs[w.x];
+  if (phase > P.pad) return;
   const int col = w.y;
   const double* bc = P.b + (size_t)col * P.n;
   const double* uc = P.u + (size_t)col * P.n;
@@ -165,7 +178,8 @@ static void batch_free(pide_batch* p) {
 
 extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
                                          const double* const* b, double* const* u,
-                                         const int32_t* Bs, pide_batch_handle* out) {
+                                         const int32_t* Bs, const int32_t* sweeps_k,
+                                         pide_batch_handle* out) {
   if (out) *out = nullptr;
   if (!out || nprob < 0 || (nprob > 0 && (!hs || !b || !u || !Bs))) {
     set_error("pide_batch_create: bad argument");
@@ -202,8 +216,9 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
       return s;
     }
     probs[k] = BatchProb{h->inv, h->w, b[k], u[k], (float*)h->R, h->ld, h->n, h->mx, Bs[k],
-                         h->prec == PIDE_FP32 ? 0 : 1, 0};
-    const int mt = (h->n + BT - 1) / BT, ct = (Bs[k] + BT - 1) / BT;
+                         h->prec == PIDE_FP32 ? 0 : 1,
+                         sweeps_k ? (sweeps_k[k] < 0 ? 0 : sweeps_k[k]) : 1 << 30};
+    const int mt = (h->n + BM - 1) / BM, ct = (Bs[k] + BT - 1) / BT;
     for (int i = 0; i < mt; ++i)
       for (int j = 0; j < ct; ++j) {
         const int cols = std::min(BT, Bs[k] - j * BT);
@@ -248,16 +263,16 @@ static pide_status batch_enqueue(pide_batch* p, int sweeps, cudaStream_t st) {
   }
   PIDE_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, (1 + sweeps) * sizeof(int), st));
   const int grid_apply = std::min(p->nitems, p->num_sms * 4);
-  batched_vec_kernel<<<p->ncolitems, 256, 0, st>>>(p->d_probs, p->d_colitems, 0);
+  batched_vec_kernel<<<p->ncolitems, 256, 0, st>>>(p->d_probs, p->d_colitems, 0, 0);
   PIDE_CUDA_TRY(cudaGetLastError());
   batched_apply_kernel<<<grid_apply, 256, 0, st>>>(p->d_probs, p->d_items, p->nitems,
-                                                   p->d_counter, 0);
+                                                   p->d_counter, 0, 0);
   PIDE_CUDA_TRY(cudaGetLastError());
   for (int k = 0; k < sweeps; ++k) {
-    batched_vec_kernel<<<p->ncolitems, 256, 0, st>>>(p->d_probs, p->d_colitems, 1);
+    batched_vec_kernel<<<p->ncolitems, 256, 0, st>>>(p->d_probs, p->d_colitems, 1, k + 1);
     PIDE_CUDA_TRY(cudaGetLastError());
     batched_apply_kernel<<<grid_apply, 256, 0, st>>>(p->d_probs, p->d_items, p->nitems,
-                                                     p->d_counter + 1 + k, 1);
+                                                     p->d_counter + 1 + k, 1, k + 1);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
   return PIDE_OK;
@@ -306,7 +321,7 @@ extern "C" pide_status pide_apply_batched_impl(const pide_handle* hs, int32_t np
                                                const double* const* b, double* const* u,
                                                const int32_t* Bs, int32_t sweeps, void* stream) {
   pide_batch_handle p = nullptr;
-  PIDE_TRY(pide_batch_create(hs, nprob, b, u, Bs, &p));
+  PIDE_TRY(pide_batch_create(hs, nprob, b, u, Bs, nullptr, &p));
   pide_status s = pide_batch_run(p, sweeps, 0, stream);
   if (s == PIDE_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) s = PIDE_ECUDA;
   batch_free(p);

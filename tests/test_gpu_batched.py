@@ -90,3 +90,26 @@ def test_batched_rejects_fp64_store():
     b = torch.zeros((2, s.n), dtype=torch.float64, device="cuda")
     with pytest.raises(PideError):
         BatchPlan([s], [b], [torch.empty_like(b)])
+
+
+def test_batch_plan_per_problem_sweeps():
+    """FP32 problems capped at 2 sweeps, BF16 at 8, in one plan."""
+    from paper_1602_00001_gb300.binding import Solver, BatchPlan
+    sides, Bs = [30, 45, 22, 37], [7, 64, 1, 20]
+    solvers, bs, us, refs, caps = [], [], [], [], []
+    for k, (side, B) in enumerate(zip(sides, Bs)):
+        h = 1.0 / (side - 1)
+        eps = W.eps_lognormal(side, side, seed=90 + k)
+        b = O.rhs_from_charge(side, side, h, eps, W.gaussian_blobs(side, side, h, 95 + k, batch=B))
+        prec = "fp32" if k % 2 == 0 else "bf16"
+        solvers.append(Solver(side, side, h, eps, prec))
+        caps.append(2 if prec == "fp32" else 8)
+        bs.append(torch.from_numpy(b).cuda())
+        us.append(torch.zeros_like(bs[-1]))
+        refs.append(O.solve(side, side, eps, b))
+    plan = BatchPlan(solvers, bs, us, sweeps_per_problem=caps)
+    plan.run(sweeps=8, use_graph=False)
+    torch.cuda.synchronize()
+    for u, r in zip(us, refs):
+        assert O.rel_error_eq6(u.cpu().numpy(), r) < 1e-6
+    plan.close()
