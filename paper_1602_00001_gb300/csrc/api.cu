@@ -67,7 +67,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-static pide_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base,
+pide_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base,
                              uint64_t inner, uint64_t outer, uint64_t row_bytes, uint32_t box_in,
                              uint32_t box_out) {
   auto fn = encode_fn();

@@ -3,17 +3,20 @@
 //
 // A plan (pide_batch_create) uploads a problem table and two device work
 // lists once:
-//   tile items  (problem, 128-row tile, 64-column tile), ordered largest work
+//   tile items  (problem, 64-row tile, 64-column tile), ordered largest work
 //               first (n_k x columns), pulled by persistent CTAs from an
 //               atomic counter -- the apply of every problem in ONE launch;
 //   column items (problem, column) -- prep and FP64 residual of every problem
-//               in one launch each.
+//               in one launch each;
+//   BF16 problems go to a grouped tcgen05 launch instead of the SIMT one:
+//               (problem, 128-row tile, 64-column tile) items whose TMA maps
+//               come from a device array of per-problem descriptors.
 // pide_batch_run then issues prep, apply, and `sweeps` x (residual, apply):
 // 2 + 2*sweeps launches for the whole set, optionally replayed from a CUDA
 // graph captured on the first run.  Each problem may cap its own sweep count
 // (an FP32 store needs fewer than a BF16 one): its items are skipped in the
 // phases past its cap.  The apply is a register-tiled FP32 SIMT contraction
-// (8 x 4 results per thread, columns contiguous per thread so warps past a
+// (4 x 4 results per thread, columns contiguous per thread so warps past a
 // problem's last column skip their arithmetic).
 #include <algorithm>
 #include <cstring>
@@ -32,10 +35,10 @@ struct BatchProb {
   float* R;             // [B][ld] FP32 right-hand side / residual
   int ld, n, mx, B, fmt;  // fmt: 0 FP32, 1 BF16
   int pad;                // sweeps this problem runs (phases past it are skipped)
+  int rbf16;              // 1: R holds BF16 for the grouped tensor-core apply, 0: FP32
 };
 
-constexpr int BM = 128;  // rows per tile item
-constexpr int BT = 64;   // columns per tile item
+constexpr int BT = 64;   // rows and columns per tile item
 constexpr int BK = 32;   // K step
 
 __device__ __forceinline__ float load_a(const BatchProb& P, size_t idx) {
@@ -43,15 +46,12 @@ __device__ __forceinline__ float load_a(const BatchProb& P, size_t idx) {
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(P.inv)[idx]);
 }
 
-// 128 x 64 output tile per item, 256 threads: thread (tx, ty) owns rows
-// 4 tx .. +3 and 64 + 4 tx .. +3 and columns 4 ty .. +3 (32 accumulators);
-// per k it reads three float4 from shared memory for 32 FMAs.
 __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __restrict__ probs,
                                                             const int4* __restrict__ items,
                                                             int nitems, int* __restrict__ counter,
                                                             int accumulate, int phase) {
-  __shared__ __align__(16) float As[BK][BM + 4];
-  __shared__ __align__(16) float Xs[BK][BT + 4];
+  __shared__ float As[BK][BT + 4];
+  __shared__ float Xs[BK][BT + 4];
   __shared__ int s_item;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   while (true) {
@@ -63,42 +63,37 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
     const int4 w = items[it];
     const BatchProb P = probs[w.x];
     if (phase > P.pad) continue;                      // this problem already ran its sweeps
-    const int p0 = w.y * BM, c0 = w.z * BT;
+    const int p0 = w.y * BT, c0 = w.z * BT;
     const int ncols = min(BT, P.B - c0);
     const bool active = ty * 4 < ncols;
-    float acc[8][4];
+    float acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (int k0 = 0; k0 < P.n; k0 += BK) {
-#pragma unroll
-      for (int q = 0; q < (BM * BK) / 256; ++q) {
-        const int e = threadIdx.x + 256 * q;
-        const int r = e / BK, kk = e % BK;
-        const int gk = k0 + kk, gp = p0 + r;
-        As[kk][r] = (gp < P.n && gk < P.n) ? load_a(P, (size_t)gp * P.ld + gk) : 0.f;
-      }
 #pragma unroll
       for (int q = 0; q < (BT * BK) / 256; ++q) {
         const int e = threadIdx.x + 256 * q;
         const int r = e / BK, kk = e % BK;
         const int gk = k0 + kk;
-        Xs[kk][r] = (r < ncols && gk < P.n) ? P.R[(size_t)(c0 + r) * P.ld + gk] : 0.f;
+        const int gp = p0 + r, gc = c0 + r;
+        As[kk][r] = (gp < P.n && gk < P.n) ? load_a(P, (size_t)gp * P.ld + gk) : 0.f;
+        Xs[kk][r] = (r < ncols && gk < P.n) ? P.R[(size_t)gc * P.ld + gk] : 0.f;
       }
       __syncthreads();
       if (active) {
-#pragma unroll 4
+#pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
-          const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][4 * tx]);
-          const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + 4 * tx]);
-          const float4 xv = *reinterpret_cast<const float4*>(&Xs[kk][4 * ty]);
-          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+          float av[4], xv[4];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
+          for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xs[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) xv[j] = Xs[kk][ty * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
         }
       }
       __syncthreads();
@@ -109,8 +104,8 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
         const int c = ty * 4 + j;
         if (c >= ncols) continue;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int p = p0 + (i < 4 ? 4 * tx + i : 64 + 4 * tx + (i - 4));
+        for (int i = 0; i < 4; ++i) {
+          const int p = p0 + tx + 16 * i;
           if (p >= P.n) continue;
           double* dst = P.u + (size_t)(c0 + c) * P.n + p;
           *dst = accumulate ? *dst + (double)acc[i][j] : (double)acc[i][j];
@@ -142,7 +137,201 @@ __global__ void __launch_bounds__(256) batched_vec_kernel(const BatchProb* __res
       if (p >= mx) r = fma(P.w[2 * n + p], uc[p - mx], r);
       if (p + mx < n) r = fma(P.w[3 * n + p], uc[p + mx], r);
     }
-    Rc[p] = (float)r;
+    if (P.rbf16) reinterpret_cast<__nv_bfloat16*>(P.R)[(size_t)col * P.ld + p] = __double2bfloat16(r);
+    else Rc[p] = (float)r;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// BF16 problems: one grouped tcgen05 launch.  Same pipeline as the main
+// tensor-core apply (TMA producer warp, single-thread MMA issuer, four
+// epilogue warps, 2 TMEM accumulators), but every (problem, 128-row tile,
+// 64-column tile) item takes its TMA maps from a device array of per-problem
+// descriptors, so problems of any size share the launch.
+struct alignas(64) GroupProb {
+  CUtensorMap tmA;      // stored L^-1 of the problem (box 64 x 128)
+  CUtensorMap tmR;      // its right-hand-side workspace (box 64 x 64)
+  double* u;
+  int n, B, num_kb, cap;
+};
+
+constexpr int GBN = 64, GSTAGES = 8;
+constexpr int G_A_BYTES = 128 * 128, G_B_BYTES = GBN * 128;
+
+__global__ void __launch_bounds__(192, 1) grouped_gemm_kernel(const GroupProb* __restrict__ probs,
+                                                              const int4* __restrict__ items,
+                                                              int nitems, int accumulate, int phase,
+                                                              uint32_t* __restrict__ flags) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + GSTAGES * G_A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + GSTAGES * G_B_BYTES);
+  uint64_t* empty = full + GSTAGES;
+  uint64_t* tfull = empty + GSTAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < GSTAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_s = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 2 * GBN);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint64_t pol_a = policy_evict_first();
+    int st = 0;
+    uint32_t ph = 0, issued = 0, issued_ph = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int4 w = items[it];
+      const GroupProb* P = probs + w.x;
+      if (phase > P->cap) continue;
+      const CUtensorMap* mA = &P->tmA;
+      const CUtensorMap* mR = &P->tmR;
+      prefetch_tmap(mA);
+      prefetch_tmap(mR);
+      for (int kb = 0; kb < P->num_kb; ++kb) {
+        if (!mbar_wait_bounded(&empty[st], ph ^ 1, abort_s)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full[st], G_A_BYTES + G_B_BYTES);
+        tma_load_2d_hint(sA + st * G_A_BYTES, mA, &full[st], kb * 64, w.y * 128, pol_a);
+        tma_load_2d(sB + st * G_B_BYTES, mR, &full[st], kb * 64, w.z * GBN);
+        issued |= 1u << st;
+        issued_ph = (issued_ph & ~(1u << st)) | (ph << st);
+        if (++st == GSTAGES) {
+          st = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    if (!ok) {
+      atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_TMA);
+      *abort_s = 1;
+      volatile int never = 0;
+      for (int q = 0; q < GSTAGES; ++q)
+        if (issued & (1u << q)) mbar_wait_bounded(&full[q], (issued_ph >> q) & 1u, &never);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GBN >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    int st = 0, acc = 0;
+    uint32_t ph = 0, acc_ph = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int4 w = items[it];
+      const GroupProb* P = probs + w.x;
+      if (phase > P->cap) continue;
+      if (!mbar_wait_bounded(&tempty[acc], acc_ph ^ 1, abort_s)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * GBN);
+      const int nkb = P->num_kb;
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait_bounded(&full[st], ph, abort_s)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(sA + st * G_A_BYTES);
+        const uint32_t b_addr = smem_u32(sB + st * G_B_BYTES);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
+                  (kb > 0 || k > 0) ? 1u : 0u);
+        mma_commit(&empty[st]);
+        if (++st == GSTAGES) {
+          st = 0;
+          ph ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit(&tfull[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_ph ^= 1;
+    }
+    if (!ok) {
+      atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_MMA);
+      *abort_s = 1;
+    }
+    mma_commit(drain);
+    volatile int never = 0;
+    if (!mbar_wait_bounded(drain, 0, &never)) atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_DRAIN);
+  } else if (warp >= 2) {
+    const int quarter = warp & 3;
+    const int row_in_tile = quarter * 32 + lane;
+    int acc = 0;
+    uint32_t acc_ph = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      const int4 w = items[it];
+      const GroupProb* P = probs + w.x;
+      if (phase > P->cap) continue;
+      bool ok = mbar_wait_bounded(&tfull[acc], acc_ph, abort_s);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(&flags[FLAG_ERROR], DEV_TIMEOUT_EPI);
+          *abort_s = 1;
+        }
+        break;
+      }
+      tc_fence_after();
+      const int n = P->n, B = P->B;
+      double* u = P->u;
+      const int p = w.y * 128 + row_in_tile;
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * GBN);
+#pragma unroll 1
+      for (int ch = 0; ch < GBN / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tbase + ch * 32, v);
+        tmem_ld_wait();
+        const int colbase = w.z * GBN + ch * 32;
+        if (p < n) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = colbase + j;
+            if (col < B) {
+              double* dst = u + (size_t)col * n + p;
+              const double val = f32_to_f64(__uint_as_float(v[j]));
+              *dst = accumulate ? *dst + val : val;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_ph ^= 1;
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 2 * GBN);
   }
 }
 
@@ -151,6 +340,10 @@ __global__ void __launch_bounds__(256) batched_vec_kernel(const BatchProb* __res
 
 struct pide_batch {
   int nprob = 0, nitems = 0, ncolitems = 0;
+  int ngitems = 0;                     // grouped tensor-core items (BF16 problems)
+  pide::GroupProb* d_gprobs = nullptr;
+  int4* d_gitems = nullptr;
+  uint32_t* d_flags = nullptr;
   pide::BatchProb* d_probs = nullptr;
   int4* d_items = nullptr;
   int2* d_colitems = nullptr;
@@ -173,6 +366,9 @@ static void batch_free(pide_batch* p) {
   if (p->d_items) cudaFree(p->d_items);
   if (p->d_colitems) cudaFree(p->d_colitems);
   if (p->d_counter) cudaFree(p->d_counter);
+  if (p->d_gprobs) cudaFree(p->d_gprobs);
+  if (p->d_gitems) cudaFree(p->d_gitems);
+  if (p->d_flags) cudaFree(p->d_flags);
   delete p;
 }
 
@@ -188,7 +384,9 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
   pide_batch* p = new pide_batch();
   std::vector<BatchProb> probs(nprob);
   struct Item { int prob, mt, ct; double cost; };
-  std::vector<Item> items;
+  std::vector<Item> items, gitems;
+  std::vector<GroupProb> gprobs;
+  std::vector<int> gindex(nprob, -1);
   std::vector<int2> colitems;
   int dev = -1;
   for (int k = 0; k < nprob; ++k) {
@@ -217,13 +415,37 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
     }
     probs[k] = BatchProb{h->inv, h->w, b[k], u[k], (float*)h->R, h->ld, h->n, h->mx, Bs[k],
                          h->prec == PIDE_FP32 ? 0 : 1,
-                         sweeps_k ? (sweeps_k[k] < 0 ? 0 : sweeps_k[k]) : 1 << 30};
-    const int mt = (h->n + BM - 1) / BM, ct = (Bs[k] + BT - 1) / BT;
-    for (int i = 0; i < mt; ++i)
-      for (int j = 0; j < ct; ++j) {
-        const int cols = std::min(BT, Bs[k] - j * BT);
-        items.push_back({k, i, j, (double)h->n * ((cols + 3) / 4)});
+                         sweeps_k ? (sweeps_k[k] < 0 ? 0 : sweeps_k[k]) : 1 << 30, 0};
+    if (h->prec == PIDE_BF16 && h->tmA_ok && Bs[k] > 0) {
+      // tensor cores: (problem, 128-row tile, 64-column tile) items with this problem's maps
+      GroupProb g;
+      std::memset(&g, 0, sizeof(g));
+      g.tmA = h->tmA;
+      pide_status es = encode_2d(&g.tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, h->R, h->n, h->ws_B,
+                                 (uint64_t)h->ld * 2, 64, GBN);
+      if (es != PIDE_OK) {
+        batch_free(p);
+        return es;
       }
+      g.u = u[k];
+      g.n = h->n;
+      g.B = Bs[k];
+      g.num_kb = (h->n + 63) / 64;
+      g.cap = probs[k].pad;
+      probs[k].rbf16 = 1;
+      gindex[k] = (int)gprobs.size();
+      gprobs.push_back(g);
+      const int mt = (h->n + 127) / 128, ct = (Bs[k] + GBN - 1) / GBN;
+      for (int i = 0; i < mt; ++i)
+        for (int j = 0; j < ct; ++j) gitems.push_back({gindex[k], i, j, (double)g.num_kb});
+    } else {
+      const int mt = (h->n + BT - 1) / BT, ct = (Bs[k] + BT - 1) / BT;
+      for (int i = 0; i < mt; ++i)
+        for (int j = 0; j < ct; ++j) {
+          const int cols = std::min(BT, Bs[k] - j * BT);
+          items.push_back({k, i, j, (double)h->n * ((cols + 3) / 4)});
+        }
+    }
     for (int c = 0; c < Bs[k]; ++c) colitems.push_back(make_int2(k, c));
     p->hs.push_back(h);
     p->num_sms = h->num_sms;
@@ -234,6 +456,11 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
                    [](const Item& a, const Item& c) { return a.cost > c.cost; });
   std::vector<int4> it4(items.size());
   for (size_t i = 0; i < items.size(); ++i) it4[i] = make_int4(items[i].prob, items[i].mt, items[i].ct, 0);
+  std::stable_sort(gitems.begin(), gitems.end(),
+                   [](const Item& a, const Item& c) { return a.cost > c.cost; });
+  std::vector<int4> g4(gitems.size());
+  for (size_t i = 0; i < gitems.size(); ++i) g4[i] = make_int4(gitems[i].prob, gitems[i].mt, gitems[i].ct, 0);
+  p->ngitems = (int)g4.size();
   p->nprob = nprob;
   p->nitems = (int)it4.size();
   p->ncolitems = (int)colitems.size();
@@ -251,29 +478,51 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
   if (!probs.empty() && (e = cudaMemcpy(p->d_probs, probs.data(), probs.size() * sizeof(BatchProb), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if (!it4.empty() && (e = cudaMemcpy(p->d_items, it4.data(), it4.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if (!colitems.empty() && (e = cudaMemcpy(p->d_colitems, colitems.data(), colitems.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if (!gprobs.empty()) {
+    if ((e = cudaMalloc((void**)&p->d_gprobs, gprobs.size() * sizeof(GroupProb))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc((void**)&p->d_gitems, g4.size() * sizeof(int4))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc((void**)&p->d_flags, FLAG_COUNT * sizeof(uint32_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(p->d_flags, 0, FLAG_COUNT * sizeof(uint32_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(p->d_gprobs, gprobs.data(), gprobs.size() * sizeof(GroupProb), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(p->d_gitems, g4.data(), g4.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    const size_t smem = 1024 + (size_t)GSTAGES * (G_A_BYTES + G_B_BYTES) + 256;
+    if ((e = cudaFuncSetAttribute(grouped_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return fail(e);
+  }
   *out = p;
   return PIDE_OK;
 }
 
+static pide_status batch_apply(pide_batch* p, int phase, cudaStream_t st) {
+  if (p->nitems > 0) {
+    const int grid_apply = std::min(p->nitems, p->num_sms * 4);
+    batched_apply_kernel<<<grid_apply, 256, 0, st>>>(p->d_probs, p->d_items, p->nitems,
+                                                     p->d_counter + phase, phase > 0, phase);
+    PIDE_CUDA_TRY(cudaGetLastError());
+  }
+  if (p->ngitems > 0) {
+    const size_t smem = 1024 + (size_t)GSTAGES * (G_A_BYTES + G_B_BYTES) + 256;
+    const int grid = std::min(p->ngitems, p->num_sms);
+    grouped_gemm_kernel<<<grid, 192, smem, st>>>(p->d_gprobs, p->d_gitems, p->ngitems, phase > 0,
+                                                 phase, p->d_flags);
+    PIDE_CUDA_TRY(cudaGetLastError());
+  }
+  return PIDE_OK;
+}
+
 static pide_status batch_enqueue(pide_batch* p, int sweeps, cudaStream_t st) {
-  if (p->nitems == 0) return PIDE_OK;
+  if (p->nitems == 0 && p->ngitems == 0) return PIDE_OK;
   if (1 + sweeps > p->counters) {
     set_error("pide_batch_run: at most 63 sweeps");
     return PIDE_EINVAL;
   }
   PIDE_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, (1 + sweeps) * sizeof(int), st));
-  const int grid_apply = std::min(p->nitems, p->num_sms * 4);
   batched_vec_kernel<<<p->ncolitems, 256, 0, st>>>(p->d_probs, p->d_colitems, 0, 0);
   PIDE_CUDA_TRY(cudaGetLastError());
-  batched_apply_kernel<<<grid_apply, 256, 0, st>>>(p->d_probs, p->d_items, p->nitems,
-                                                   p->d_counter, 0, 0);
-  PIDE_CUDA_TRY(cudaGetLastError());
+  PIDE_TRY(batch_apply(p, 0, st));
   for (int k = 0; k < sweeps; ++k) {
     batched_vec_kernel<<<p->ncolitems, 256, 0, st>>>(p->d_probs, p->d_colitems, 1, k + 1);
     PIDE_CUDA_TRY(cudaGetLastError());
-    batched_apply_kernel<<<grid_apply, 256, 0, st>>>(p->d_probs, p->d_items, p->nitems,
-                                                     p->d_counter + 1 + k, 1, k + 1);
-    PIDE_CUDA_TRY(cudaGetLastError());
+    PIDE_TRY(batch_apply(p, k + 1, st));
   }
   return PIDE_OK;
 }

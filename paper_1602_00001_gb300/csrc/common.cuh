@@ -162,6 +162,9 @@ pide_status launch_scale_d(pide_ctx* c, const double* mu, double* db, int B, cud
 
 pide_status ensure_workspace(pide_ctx* c, int B);
 pide_status make_tma_maps(pide_ctx* c);
+// 2-D tiled TMA map, 128-byte swizzle, zero fill out of bounds.
+pide_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                      uint64_t outer, uint64_t row_bytes, uint32_t box_in, uint32_t box_out);
 pide_status make_tma_rhs(pide_ctx* c, int bn);
 
 // event profiling around one launch of class `cls`
