@@ -233,7 +233,8 @@ def batched_workload(args):
         for sv, b, u, kc in zip(solvers, bs, us, caps):
             sv.apply(b, u, sweeps=kc)
     ms_loop = _evt_time(loop, max(3, args.steps // 4))
-    launches = 2 + 2 * sweeps
+    kinds = int(any(sv.precision == "fp32" for sv in solvers)) + int(any(sv.precision == "bf16" for sv in solvers))
+    launches = 1 + (1 + sweeps) * kinds + sweeps
     line = {"metric": "RHS solves/s, 64 uneven grids (batched)", "value": total_rhs / (ms_batched * 1e-3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": ms_batched,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32+bf16",

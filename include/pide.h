@@ -142,7 +142,9 @@ pide_status pide_apply(pide_handle h, const double* b_dev, double* u_dev, int32_
 /*
  * pide_apply_host -- pide_apply on HOST buffers: copies b to the device,
  * applies, copies u back and synchronises.  b_host/u_host are [B][n] float64
- * (pinned memory makes the copies asynchronous-capable and fast).
+ * (pinned memory makes the copies asynchronous-capable and fast).  For
+ * B >= 512 with tol <= 0 and no info, the columns go in two chunks and the
+ * copies of one chunk run on an internal stream under the other's solve.
  */
 pide_status pide_apply_host(pide_handle h, const double* b_host, double* u_host, int32_t B,
                             int32_t max_sweeps, double tol, void* stream, pide_info* info);

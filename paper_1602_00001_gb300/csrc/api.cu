@@ -327,6 +327,8 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   PIDE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
   PIDE_CUDA_TRY(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_lo));
   for (int k = 0; k < 6; ++k) PIDE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
+  PIDE_CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+  for (int k = 0; k < 6; ++k) PIDE_CUDA_TRY(cudaEventCreateWithFlags(&c->hev[k], cudaEventDisableTiming));
   PIDE_CUDA_TRY(cudaMemcpyAsync(c->eps, c->eps_host.data(), N * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
   PIDE_TRY(launch_assemble(c, st));
@@ -416,7 +418,10 @@ extern "C" void pide_destroy(pide_handle h) {
   }
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->hev)
+    if (e) cudaEventDestroy(e);
   if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   delete h;
 }
 
@@ -468,6 +473,34 @@ extern "C" pide_status pide_apply_host(pide_handle h, const double* b_host, doub
     h->hbuf_B = B;
   }
   const size_t bytes = (size_t)B * h->n * sizeof(double);
+  if (B >= 512 && tol <= 0 && !info && h->cstream) {
+    // Two column chunks: the copy stream moves chunk 1 in while chunk 0 is
+    // solved, and chunk 0 out while chunk 1 is solved.
+    const int B0 = ((B / 2 + 127) / 128) * 128;
+    const int c0[2] = {0, B0}, cn[2] = {B0, B - B0};
+    cudaEvent_t fork = h->hev[0], in[2] = {h->hev[1], h->hev[2]}, done[2] = {h->hev[3], h->hev[4]},
+                out = h->hev[5];
+    PIDE_CUDA_TRY(cudaEventRecord(fork, st));
+    PIDE_CUDA_TRY(cudaStreamWaitEvent(h->cstream, fork, 0));
+    for (int q = 0; q < 2; ++q) {
+      const size_t off = (size_t)c0[q] * h->n;
+      PIDE_CUDA_TRY(cudaMemcpyAsync(h->hbuf_b + off, b_host + off, (size_t)cn[q] * h->n * sizeof(double),
+                                    cudaMemcpyHostToDevice, h->cstream));
+      PIDE_CUDA_TRY(cudaEventRecord(in[q], h->cstream));
+    }
+    for (int q = 0; q < 2; ++q) {
+      const size_t off = (size_t)c0[q] * h->n;
+      PIDE_CUDA_TRY(cudaStreamWaitEvent(st, in[q], 0));
+      PIDE_TRY(solve_s(h, h->hbuf_b + off, 0, nullptr, h->hbuf_u + off, cn[q], max_sweeps, tol, st));
+      PIDE_CUDA_TRY(cudaEventRecord(done[q], st));
+      PIDE_CUDA_TRY(cudaStreamWaitEvent(h->cstream, done[q], 0));
+      PIDE_CUDA_TRY(cudaMemcpyAsync(u_host + off, h->hbuf_u + off, (size_t)cn[q] * h->n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->cstream));
+    }
+    PIDE_CUDA_TRY(cudaEventRecord(out, h->cstream));
+    PIDE_CUDA_TRY(cudaStreamWaitEvent(st, out, 0));
+    return check_device_error(h, st);
+  }
   PIDE_CUDA_TRY(cudaMemcpyAsync(h->hbuf_b, b_host, bytes, cudaMemcpyHostToDevice, st));
   PIDE_TRY(solve_s(h, h->hbuf_b, 0, nullptr, h->hbuf_u, B, max_sweeps, tol, st));
   PIDE_CUDA_TRY(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, st));

@@ -96,6 +96,8 @@ struct pide_ctx {
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
   cudaStream_t aux = nullptr;       // low-priority stream for the overlapped residuals
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t cstream = nullptr;   // host<->device copies of pide_apply_host
+  cudaEvent_t hev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
   int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8

@@ -195,6 +195,23 @@ def test_apply_host_matches_device():
     assert np.max(np.abs(ud - uh)) <= 1e-14 * np.max(np.abs(ud))
 
 
+def test_apply_host_pipelined_chunks():
+    """B >= 512: host copies overlap the solves of two column chunks; same
+    answer as the device apply (up to the chunked GEMM's FP32 rounding)."""
+    nx = ny = 34
+    h = 1.0 / 33
+    eps = W.eps_lognormal(nx, ny, seed=19)
+    b = _b(nx, ny, h, eps, 700, seed=4)
+    s = _solver(nx, ny, h, eps, "bf16")
+    ud = s.apply(b, sweeps=5).cpu().numpy()
+    bh = torch.from_numpy(b).pin_memory()
+    uh = torch.empty_like(bh).pin_memory()
+    s.apply_host(bh, uh, sweeps=5)
+    ref = O.solve(nx, ny, eps, b, route="band")
+    assert O.rel_error_eq6(uh.numpy(), ref) < 1e-6
+    assert np.max(np.abs(uh.numpy() - ud)) <= 1e-8 * np.max(np.abs(ud))
+
+
 def test_save_load_roundtrip(tmp_path):
     nx, ny = 26, 21
     h = 1.0 / 25
