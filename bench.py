@@ -244,9 +244,24 @@ def batched_workload(args):
                        "sizes": [int(p[0]) for p in probs]},
             "per_problem_loop": {"ms_per_step": ms_loop, "value": total_rhs / (ms_loop * 1e-3)},
             "speedup_vs_loop": ms_loop / ms_batched, "gpu_launches_per_step": launches,
+            "roofline": batched_roofline(solvers, bs, caps, ms_batched),
             "accuracy": {"max_rel_err_eq6_vs_oracle_4_problems": max(errs)}}
     print(json.dumps(line))
     return 0
+
+
+def batched_roofline(solvers, bs, caps, ms):
+    """HBM view of a batched step: every apply streams each problem's stored
+    inverse once (BF16 2 B, FP32 4 B per entry); 1 + cap applies per problem."""
+    pk, kind = peaks()
+    byts = 0.0
+    for sv, b, cap in zip(solvers, bs, caps):
+        esz = 4 if sv.precision == "fp32" else 2
+        byts += (1 + cap) * sv.n * sv.n * esz
+    gbs = byts / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / pk["hbm_gbs"], "traffic": None,
+            "note": "algorithmic inverse bytes over all applies of the step; FP32 problems run on the SIMT pipe"}
 
 
 def adjoint_workload(args):
@@ -283,7 +298,11 @@ def adjoint_workload(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic", "config": {"workload": "128x128 nodes, lognormal eps, B=32",
                                             "sweeps": sweeps},
-            "accuracy": {"db_rel_err_vs_oracle": err_db, "deps_rel_err_vs_oracle": err_de}}
+            "accuracy": {"db_rel_err_vs_oracle": err_db, "deps_rel_err_vs_oracle": err_de},
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks()[0]["hbm_gbs"],
+                         "achieved": 2 * (1 + sweeps) * s.info().store_bytes / (ms * 1e-3) / 1e9,
+                         "note": "B = 32 is HBM-bound: forward and adjoint solves each stream the BF16 inverse 1 + sweeps times"}}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     print(json.dumps(line))
     return 0
 
