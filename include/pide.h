@@ -270,7 +270,15 @@ pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
  *                           triangle of the symmetric S^-1 (L^-1 = S^-1 D) in two BF16 terms,
  *                           ~16 significant bits for the bytes of the one-term L^-1, so
  *                           refinement needs about a quarter of the sweeps;
- *                           0: through the one-term L^-1 (GEMV) */
+ *                           0: through the one-term L^-1 (GEMV)
+ *   PIDE_TUNE_RESID_EMUL    1 (default): BF16 / FP8 / FP8X2 handles evaluate the refinement
+ *                           residual (forward mode, and the BF16 prep) on the integer and
+ *                           FP32 pipes: each FP64 input split into two floats (47
+ *                           significant bits), the stencil in error-free float arithmetic,
+ *                           absolute error ~2^-45 (|u_p| + sum_q w_pq |u_q|); skipped when
+ *                           0 < tol < 1e-8, where only the FP64 stencil resolves the residual.
+ *                           0: the FP64 stencil always.  pide_residual and the rel_residual
+ *                           of pide_info are always FP64. */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -279,7 +287,8 @@ typedef enum {
   PIDE_TUNE_GEMM_STREAMK = 4,
   PIDE_TUNE_OVERLAP = 5,
   PIDE_TUNE_RESID_CTAS = 6,
-  PIDE_TUNE_SYMV = 7
+  PIDE_TUNE_SYMV = 7,
+  PIDE_TUNE_RESID_EMUL = 8
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);
@@ -294,6 +303,13 @@ pide_status pide_selftest_wait_timeout(int64_t budget_cycles, void* stream);
 /* Conversion self test: for n device inputs, writes the library's own
  * integer-pipe conversions (binary64 -> bfloat16 round-to-nearest-even bits,
  * binary32 -> binary64) beside CUDA's, so a test can compare them bit for bit. */
+/* Residual self test: the double-float residual kernel the refinement uses
+ * (PIDE_TUNE_RESID_EMUL), r = f - L u with f = b (+ the lift of the boundary
+ * values g_dev[ny*nx], or none when NULL), written as FP32 to r_dev[B][n] so
+ * a test can compare it with the exact residual.  Device buffers, stream-ordered. */
+pide_status pide_selftest_residual_df(pide_handle h, const double* b_dev, const double* u_dev,
+                                      const double* g_dev, float* r_dev, int32_t B, void* stream);
+
 pide_status pide_selftest_convert(const double* x_dev, const float* f_dev, int64_t n,
                                   uint16_t* bf_mine, uint16_t* bf_cuda, double* d_mine,
                                   double* d_cuda, void* stream);

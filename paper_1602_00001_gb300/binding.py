@@ -74,6 +74,7 @@ _SIGS = {
     "pide_get_tuning": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "pide_selftest_wait_timeout": (_I, [ctypes.c_int64, _P]),
     "pide_selftest_convert": (_I, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
+    "pide_selftest_residual_df": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "pide_status_string": (ctypes.c_char_p, [_I]),
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),
@@ -217,6 +218,21 @@ class Solver:
                                       _stream(stream)), "pide_residual")
         return r
 
+    def residual_df(self, b, u, g=None, stream=None):
+        """The refinement's double-float residual as FP32 (test hook; see pide.h)."""
+        import torch
+        b = _as_dev(b, self.device).reshape(-1, self.n)
+        u = _as_dev(u, self.device).reshape(-1, self.n)
+        gp = None
+        if g is not None:
+            g = _as_dev(g, self.device).reshape(-1)
+            gp = _ptr(g)
+        r = torch.empty(b.shape, dtype=torch.float32, device=b.device)
+        _check(self.lib.pide_selftest_residual_df(self.handle, _ptr(b), _ptr(u), gp, _ptr(r),
+                                                  b.shape[0], _stream(stream)),
+               "pide_selftest_residual_df")
+        return r
+
     def rhs_from_charge(self, rho, stream=None):
         import torch
         rho = _as_dev(rho, self.device).reshape(-1, self.n)
@@ -239,7 +255,8 @@ class Solver:
         return db, deps
 
     TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3,
-                 "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6, "symv": 7}
+                 "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6, "symv": 7,
+                 "resid_emul": 8}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

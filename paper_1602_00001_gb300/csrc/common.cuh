@@ -61,6 +61,7 @@ struct pide_ctx {
   double* d = nullptr;              // [n] diagonal of S (sum of face eps)
   double* dinv = nullptr;           // [n] 1 / d
   double* w = nullptr;              // [4][n] Eq. (3) weights w = cf / d
+  float4* wsp = nullptr;            // [2][n] w as float pairs (hi, lo), zero toward boundary nodes
   std::vector<double> eps_host;     // kept for save/load
   // stored inverse L^-1 = S^-1 D (the interior block of the Fig. 3 inverse)
   void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / e4m3 (hi)
@@ -102,6 +103,7 @@ struct pide_ctx {
   int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8
   int symv = 1;                     // B = 1 through the packed symmetric S^-1 (half the bytes)
+  int resid_emul = 1;               // refinement residual in double-float (off the FP64 pipe)
   // profiling
   bool prof_on = false;
   struct Ev { cudaEvent_t a, b; int cls; };
@@ -121,18 +123,29 @@ pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st);   // G 
 pide_status quantize_store(pide_ctx* c, const double* G, cudaStream_t st);
 
 // RHS preparation: R = q(f), f = b + lift (mode 0) or f = b / d (mode 1, adjoint).
+// emul: BF16 forward prep through the integer/FP32 pipes (same codes as FP64).
 pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
-                        int rfmt, bool track, cudaStream_t st);
+                        int rfmt, bool track, cudaStream_t st, bool emul = false);
 // Residual: R = q(f - L u) (FP64 stencil); optional column max of |r| into colmax.
 // col0: first column of a column group (b, u, R rows, scales and maxima offset by it).
+// emul: forward residuals written only to R take the double-float kernel.
 pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
-                            bool honor_done, cudaStream_t st, int col0 = 0);
+                            bool honor_done, cudaStream_t st, int col0 = 0, bool emul = false);
 pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
 // FP8 right-hand sides in one FP64 pass: residual to FP32 scratch with the column
 // maxima, per-column scale, then e4m3 quantisation of the scratch into R.
 pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, int B, int mode,
-                                const double* lift, cudaStream_t st);
+                                const double* lift, cudaStream_t st, bool emul = false);
+// Double-float residual (residual_df.cu): weights split once per operator, then
+// r = f - L u (forward mode) into R[B][ldr] as BF16 / FP32 / e4m3 (col_scale).
+pide_status launch_wsplit(pide_ctx* c, cudaStream_t st);
+pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, int B,
+                               const double* lift, int rfmt, void* R, int ldr,
+                               const float* col_scale, double* colmax_r, bool track,
+                               const uint32_t* flags, cudaStream_t st);
+pide_status launch_prep_df_bf16(pide_ctx* c, const double* b, int B, const double* lift,
+                                bool track, cudaStream_t st);
 // Residual with a small persistent grid (num_sms * resid_ctas_per_sm blocks), for the
 // overlapped schedule; writes R only.
 pide_status launch_residual_persistent(pide_ctx* c, const double* b, const double* u, int B,

@@ -328,9 +328,10 @@ static dim3 col_grid(int n, int B) {
 }
 
 pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const double* lift,
-                        int rfmt, bool track, cudaStream_t st) {
+                        int rfmt, bool track, cudaStream_t st, bool emul) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 2);
+  if (emul && mode == 0 && rfmt == RF_BF16) return launch_prep_df_bf16(c, b, B, lift, track, st);
   dim3 g = col_grid(c->n, B);
   double* cmb = c->colmax + c->ws_B;
   const int t = track ? 1 : 0;
@@ -346,7 +347,7 @@ pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const dou
 
 pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B, int mode,
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
-                            bool honor_done, cudaStream_t st, int col0) {
+                            bool honor_done, cudaStream_t st, int col0, bool emul) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 1);
   dim3 g = col_grid(c->n, B);
@@ -358,6 +359,9 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
   const uint32_t* fl = honor_done ? c->flags : nullptr;
   double* cm = c->colmax + col0;
   const int t = track ? 1 : 0;
+  if (emul && mode == 0 && R && !r_out && rfmt != RF_F64)
+    return launch_residual_df(c, b, u, B, lift, rfmt, R, c->ld,
+                              rfmt == RF_E4M3 ? c->col_scale + col0 : nullptr, cm, track, fl, st);
   switch (rfmt) {
     case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
@@ -473,13 +477,18 @@ __global__ void quantize_e4m3_kernel(const float* __restrict__ Rf, int n, int ld
 }  // namespace
 
 pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, int B, int mode,
-                                const double* lift, cudaStream_t st) {
+                                const double* lift, cudaStream_t st, bool emul) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 1);
   dim3 g = col_grid(c->n, B);
   double* raw = c->colmax + 2 * (size_t)c->ws_B;
-  residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift,
-                                             c->Rf, nullptr, nullptr, raw, 1, c->flags);
+  if (emul && mode == 0) {
+    PIDE_TRY(launch_residual_df(c, b, u, B, lift, RF_F32, c->Rf, c->ld, nullptr, raw, true,
+                                c->flags, st));
+  } else {
+    residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv,
+                                               lift, c->Rf, nullptr, nullptr, raw, 1, c->flags);
+  }
   PIDE_CUDA_TRY(cudaGetLastError());
   finalize_scale_kernel<<<(B + 255) / 256, 256, 0, st>>>(raw, c->col_scale, B, c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());
