@@ -278,7 +278,9 @@ pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
  *                           absolute error ~2^-45 (|u_p| + sum_q w_pq |u_q|); skipped when
  *                           0 < tol < 1e-8, where only the FP64 stencil resolves the residual.
  *                           0: the FP64 stencil always.  pide_residual and the rel_residual
- *                           of pide_info are always FP64. */
+ *                           of pide_info are always FP64.
+ *   PIDE_TUNE_RESID_SHAPE   launch shape of that residual kernel, consecutive nodes x columns
+ *                           per thread: 0 (default) 4 x 2, 1: 4 x 1, 2: 2 x 2, 3: 2 x 1 */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -288,7 +290,8 @@ typedef enum {
   PIDE_TUNE_OVERLAP = 5,
   PIDE_TUNE_RESID_CTAS = 6,
   PIDE_TUNE_SYMV = 7,
-  PIDE_TUNE_RESID_EMUL = 8
+  PIDE_TUNE_RESID_EMUL = 8,
+  PIDE_TUNE_RESID_SHAPE = 9
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -21,18 +21,20 @@ namespace pide {
 namespace {
 
 // x = h + l with h = x truncated to 24 significant bits and l = the next 23
-// bits (47 in all); x = 0 gives h = l = 0.  Integer operations and one FP32
-// subtraction.  Returns false when x != 0 lies outside 2^-103 <= |x| < 2^128.
+// bits (47 in all): integer operations and one FP32 subtraction.  Returns
+// the binary64 exponent field E of x.  Inputs with E < 920 (|x| < 2^-103,
+// including 0) give h = l = 0; the split is exact to 47 bits for
+// 920 <= E <= 1150 (|x| < 2^128); above that the caller takes the FP64 route.
 // With sticky = true the dropped low bits set the last bit of l (round to
 // odd), so that a later rounding of h + l to 8 or 24 bits equals the
 // rounding of x itself.
 template <bool sticky>
-__device__ __forceinline__ bool split47(double x, float& h, float& l) {
+__device__ __forceinline__ uint32_t split47(double x, float& h, float& l) {
   const uint64_t bits = (uint64_t)__double_as_longlong(x);
   const uint32_t hi = (uint32_t)(bits >> 32), lo = (uint32_t)bits;
-  // exponent field E (11 bits) and the top 23 fraction bits, shifted so that
-  // E's low 9 bits land on binary32's exponent field; E - 896 rebiases
-  // 1023 -> 127 (adding 128 is the same modulo 512)
+  // the exponent field's low 9 bits and the top 23 fraction bits, shifted onto
+  // binary32's fields; E - 896 rebiases 1023 -> 127 (adding 128 is the same
+  // modulo 512)
   const uint32_t t = __funnelshift_l(lo, hi, 3);
   const uint32_t hb = ((t + 0x40000000u) & 0x7FFFFFFFu) | (hi & 0x80000000u);
   // l: the 29 fraction bits below h, top 23 of them, as 2^(e_h - 23) * q / 2^23
@@ -41,12 +43,28 @@ __device__ __forceinline__ bool split47(double x, float& h, float& l) {
   if (sticky) q |= (lo & 0x3Fu) ? 1u : 0u;
   const float hh = __uint_as_float(hb);
   const float ll = __fsub_rn(__uint_as_float(base | q), __uint_as_float(base));
-  const bool zero = (bits << 1) == 0;
-  h = zero ? 0.f : hh;
-  l = zero ? 0.f : ll;
   const uint32_t e = (hi >> 20) & 0x7FFu;
-  return zero || (e - 920u <= 230u);
+  const bool tiny = e < 920u;
+  h = tiny ? 0.f : hh;
+  l = tiny ? 0.f : ll;
+  return e;
 }
+
+// As split47, with inputs at or above 2^128 (and Inf, NaN) marked as h = NaN:
+// a stencil that touches one gives a NaN result and takes the FP64 route.
+__device__ __forceinline__ void split_marked(double x, float& h, float& l) {
+  float hh, ll;
+  const uint32_t e = split47<false>(x, hh, ll);
+  h = e > 1150u ? __int_as_float(0x7FC00000) : hh;
+  l = ll;
+}
+
+// Exponent-field limits of the fast route.  A node is evaluated in
+// double-float when none of its inputs reaches 2^128 (E <= 1150) and its own
+// scale max(|f_p|, |u_p|) is at least 2^-60 (E >= 963): the inputs below
+// 2^-103 that the split drops then change r by at most 2^-102, within the
+// 2^-42 (|f_p| + |u_p| + ...) error bound.  Other nodes take the FP64 formula.
+constexpr uint32_t E_SPLIT_MAX = 1150u, E_NODE_MIN = 963u;
 
 // (sh, sl) += (ah, al); two-sum of the high parts, low parts added.
 __device__ __forceinline__ void df_add(float& sh, float& sl, float ah, float al) {
@@ -67,7 +85,7 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float wh, float wl,
   df_add(sh, sl, ph, pl);
 }
 
-// bfloat16 bits of s + e rounded to nearest even, for s = fl(s + e) and
+// bfloat16 of s + e rounded to nearest even, for s = fl(s + e) and
 // |e| <= ulp(s) / 2: s's own rounding is right unless s sits exactly half-way
 // between two bfloat16 values, where the sign of e decides.
 __device__ __forceinline__ __nv_bfloat16 bf16_of_pair(float s, float e) {
@@ -75,6 +93,33 @@ __device__ __forceinline__ __nv_bfloat16 bf16_of_pair(float s, float e) {
   if ((x & 0xFFFFu) == 0x8000u && e != 0.f)
     x += (((__float_as_uint(e) ^ x) >> 31) != 0u) ? 0xFFFFFFFFu : 1u;
   return __float2bfloat16_rn(__uint_as_float(x));
+}
+
+// The FP64 formula for one node (out-of-range inputs).  Not inlined, so that
+// the fast route's warps never issue its FP64 instructions.
+__device__ __noinline__ double residual_node_fp64(const double* __restrict__ bc,
+                                                  const double* __restrict__ uc,
+                                                  const double* __restrict__ w4,
+                                                  const double* __restrict__ lift, int n, int mx,
+                                                  int p) {
+  const int c = p % mx;
+  double r = lift ? bc[p] + (lift[p] - uc[p]) : bc[p] - uc[p];
+  if (c > 0) r = fma(w4[p], uc[p - 1], r);
+  if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
+  if (p >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
+  if (p + mx < n) r = fma(w4[3 * n + p], uc[p + mx], r);
+  return r;
+}
+
+__device__ __noinline__ void split_f64_slow(double r, float& s, float& e) {
+  s = __double2float_rn(r);
+  e = __double2float_rn(r - (double)s);
+}
+
+__device__ __noinline__ __nv_bfloat16 bf16_of_f64_slow(double v) { return __double2bfloat16(v); }
+
+__device__ __forceinline__ bool is_zero(double x) {
+  return ((uint64_t)__double_as_longlong(x) << 1) == 0;
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
@@ -111,13 +156,22 @@ __global__ void wsplit_kernel(const double* __restrict__ w4, int n, int mx,
   }
 }
 
-constexpr int DF_COLS = 2;   // columns per thread: the weights are loaded once for both
+// Launch shapes of the shared-memory kernel (PIDE_TUNE_RESID_SHAPE): SM_NR
+// nodes per thread (a tile of 256 * SM_NR nodes per block), SM_COLS columns
+// per block (the weights loaded once for all of them).
+constexpr int SM_SHAPES[4][2] = {{4, 2}, {8, 2}, {4, 1}, {8, 1}};
+constexpr size_t SMEM_MAX = 48 * 1024;   // larger halos (very wide grids) take the register kernel
 
-// r = f - u_p + sum_q w_pq u_q for columns blockIdx.y * DF_COLS + k, written to R
-// (BF16 rounded to nearest from the pair, FP32, or e4m3 after the column scale);
-// optionally max |r| per column into colmax_r.
-template <int RF>
-__global__ void __launch_bounds__(256) residual_df_kernel(
+__device__ __forceinline__ int clampi(int q, int n) { return q < 0 ? 0 : (q >= n ? n - 1 : q); }
+
+// Register kernel (grids too wide for the shared-memory halo):
+// r = f - u_p + sum_q w_pq u_q for nodes p0 .. p0 + DF_NR - 1 (flat index; a
+// grid row's end needs no test since the weights toward boundary nodes are
+// zero) of columns blockIdx.y * DF_COLS + k, written to R (BF16 rounded to
+// nearest from the pair, FP32, or e4m3 after the column scale); optionally
+// max |r| per column into colmax_r.
+template <int RF, int DF_NR, int DF_COLS>
+__global__ void __launch_bounds__(256, 2) residual_df_reg_kernel(
     const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int B, int ldr,
     const float4* __restrict__ wh4, const float4* __restrict__ wl4,
     const double* __restrict__ w4, const double* __restrict__ lift, void* __restrict__ R,
@@ -132,50 +186,61 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
     isc[k] = (RF == RF_E4M3 && cbase + k < B) ? 1.0f / col_scale[cbase + k] : 1.0f;
     mxr[k] = 0.f;
   }
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const float4 wh = wh4[p], wl = wl4[p];
-    const int pw = p > 0 ? p - 1 : p, pe = p + 1 < n ? p + 1 : p;
-    const int ps = p >= mx ? p - mx : p, pn = p + mx < n ? p + mx : p;
-    float lh = 0.f, ll = 0.f;
-    const bool lok = lift ? split47<false>(lift[p], lh, ll) : true;
+  const int stride = DF_NR * gridDim.x * blockDim.x;
+  for (int p0 = DF_NR * (blockIdx.x * blockDim.x + threadIdx.x); p0 < n; p0 += stride) {
+    float4 wh[DF_NR], wl[DF_NR];
+    float lh[DF_NR], ll[DF_NR];
+    uint32_t el[DF_NR];
 #pragma unroll
-    for (int k = 0; k < DF_COLS; ++k) {
-      const int col = cbase + k;
+    for (int k = 0; k < DF_NR; ++k) {
+      const int p = clampi(p0 + k, n);
+      wh[k] = wh4[p];
+      wl[k] = wl4[p];
+      el[k] = lift ? split47<false>(lift[p], lh[k], ll[k]) : 0u;
+      if (!lift) lh[k] = ll[k] = 0.f;
+    }
+#pragma unroll
+    for (int cc = 0; cc < DF_COLS; ++cc) {
+      const int col = cbase + cc;
       if (col >= B) break;
       const double* uc = u + (size_t)col * n;
-      const double bp = b[(size_t)col * n + p];
-      const double u0 = uc[p], uw = uc[pw], ue = uc[pe], us = uc[ps], un = uc[pn];
-      float bh, bl, h0, l0, hw, lw, he, le, hs, ls, hn, ln;
-      bool ok = split47<false>(bp, bh, bl);
-      ok &= split47<false>(u0, h0, l0);
-      ok &= split47<false>(uw, hw, lw);
-      ok &= split47<false>(ue, he, le);
-      ok &= split47<false>(us, hs, ls);
-      ok &= split47<false>(un, hn, ln);
-      float s, e;
-      if (ok && lok) {
-        float sh = bh, sl = bl;
-        if (lift) df_add(sh, sl, lh, ll);
-        df_add(sh, sl, -h0, -l0);
-        df_fma(sh, sl, wh.x, wl.x, hw, lw);
-        df_fma(sh, sl, wh.y, wl.y, he, le);
-        df_fma(sh, sl, wh.z, wl.z, hs, ls);
-        df_fma(sh, sl, wh.w, wl.w, hn, ln);
-        s = __fadd_rn(sh, sl);
-        e = __fsub_rn(sl, __fsub_rn(s, sh));
-      } else {
-        // outside the split's range: the FP64 formula
-        const int c = p % mx;
-        double r = lift ? bp + (lift[p] - u0) : bp - u0;
-        if (c > 0) r = fma(w4[p], uw, r);
-        if (c < mx - 1) r = fma(w4[n + p], ue, r);
-        if (p >= mx) r = fma(w4[2 * n + p], us, r);
-        if (p + mx < n) r = fma(w4[3 * n + p], un, r);
-        s = __double2float_rn(r);
-        e = __double2float_rn(r - (double)s);
+      const double* bc = b + (size_t)col * n;
+      // row values u[p0 - 1 .. p0 + DF_NR], the rows below and above, and b
+      float rh[DF_NR + 2], rl[DF_NR + 2], sh_[DF_NR], sl_[DF_NR], nh[DF_NR], nl[DF_NR];
+      float bh[DF_NR], bl[DF_NR];
+      uint32_t er[DF_NR + 2], es[DF_NR], en[DF_NR], eb[DF_NR];
+#pragma unroll
+      for (int j = 0; j < DF_NR + 2; ++j) er[j] = split47<false>(uc[clampi(p0 - 1 + j, n)], rh[j], rl[j]);
+#pragma unroll
+      for (int k = 0; k < DF_NR; ++k) {
+        es[k] = split47<false>(uc[clampi(p0 + k - mx, n)], sh_[k], sl_[k]);
+        en[k] = split47<false>(uc[clampi(p0 + k + mx, n)], nh[k], nl[k]);
+        eb[k] = split47<false>(bc[clampi(p0 + k, n)], bh[k], bl[k]);
       }
-      store_r<RF>(R, (size_t)col * ldr + p, s, e, isc[k]);
-      if (track) mxr[k] = fmaxf(mxr[k], fabsf(s));
+#pragma unroll
+      for (int k = 0; k < DF_NR; ++k) {
+        const int p = p0 + k;
+        if (p >= n) break;
+        const uint32_t emax = max(max(max(er[k], er[k + 1]), max(er[k + 2], es[k])),
+                                  max(max(en[k], eb[k]), el[k]));
+        const uint32_t enode = max(max(er[k + 1], eb[k]), el[k]);
+        float s, e;
+        if (emax <= E_SPLIT_MAX && enode >= E_NODE_MIN) {
+          float ah = bh[k], al = bl[k];
+          if (lift) df_add(ah, al, lh[k], ll[k]);
+          df_add(ah, al, -rh[k + 1], -rl[k + 1]);
+          df_fma(ah, al, wh[k].x, wl[k].x, rh[k], rl[k]);
+          df_fma(ah, al, wh[k].y, wl[k].y, rh[k + 2], rl[k + 2]);
+          df_fma(ah, al, wh[k].z, wl[k].z, sh_[k], sl_[k]);
+          df_fma(ah, al, wh[k].w, wl[k].w, nh[k], nl[k]);
+          s = __fadd_rn(ah, al);
+          e = __fsub_rn(al, __fsub_rn(s, ah));
+        } else {
+          split_f64_slow(residual_node_fp64(bc, uc, w4, lift, n, mx, p), s, e);
+        }
+        store_r<RF>(R, (size_t)col * ldr + p, s, e, isc[cc]);
+        if (track) mxr[cc] = fmaxf(mxr[cc], fabsf(s));
+      }
     }
   }
   if (track) {
@@ -195,9 +260,119 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
   }
 }
 
-// Prep for BF16 right-hand sides, forward mode: R = bf16(b + lift), rounded to
-// nearest from the exact pair (the sticky split makes the 47-bit pair round
-// like the FP64 value); optionally max |f| per column.
+// Shared-memory kernel: block (x, y) takes the tile of T = 256 * SM_NR nodes
+// from P0 = x * T and SM_COLS columns from y * SM_COLS.  It stages u over
+// [P0 - mx - 1, P0 + T + mx + 1) (the tile and one grid row of halo on each
+// side; zero outside 0..n-1) into shared memory as split float pairs, so each
+// value is split once, then thread t evaluates nodes P0 + t + 256 k: the five
+// stencil values are consecutive-per-lane shared loads (no bank conflicts).
+// The fast route needs max(|f_p|, |u_p|) >= 2^-60 and a finite result (a
+// value at or above 2^128 is staged as NaN); other nodes take the FP64 route.
+template <int RF, int SM_NR, int SM_COLS>
+__global__ void __launch_bounds__(256) residual_df_kernel(
+    const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int B, int ldr,
+    const float4* __restrict__ wh4, const float4* __restrict__ wl4,
+    const double* __restrict__ w4, const double* __restrict__ lift, void* __restrict__ R,
+    const float* __restrict__ col_scale, double* __restrict__ colmax_r, int track,
+    const uint32_t* __restrict__ flags) {
+  extern __shared__ float2 su[];   // [SM_COLS][L]
+  __shared__ float red[SM_COLS][8];
+  if (flags && flags[FLAG_DONE]) return;
+  constexpr int T = 256 * SM_NR;
+  const int L = T + 2 * mx + 2;
+  const int P0 = blockIdx.x * T;
+  const int q0 = P0 - mx - 1;
+  const int cbase = blockIdx.y * SM_COLS;
+#pragma unroll
+  for (int cc = 0; cc < SM_COLS; ++cc) {
+    const int col = cbase + cc;
+    if (col >= B) break;
+    const double* uc = u + (size_t)col * n;
+    for (int i = threadIdx.x; i < L; i += 256) {
+      const int q = q0 + i;
+      float h = 0.f, l = 0.f;
+      if (q >= 0 && q < n) split_marked(uc[q], h, l);
+      su[cc * L + i] = make_float2(h, l);
+    }
+  }
+  __syncthreads();
+  float isc[SM_COLS], mxr[SM_COLS];
+#pragma unroll
+  for (int cc = 0; cc < SM_COLS; ++cc) {
+    isc[cc] = (RF == RF_E4M3 && cbase + cc < B) ? 1.0f / col_scale[cbase + cc] : 1.0f;
+    mxr[cc] = 0.f;
+  }
+#pragma unroll 2
+  for (int k = 0; k < SM_NR; ++k) {
+    const int p = P0 + (int)threadIdx.x + 256 * k;
+    if (p >= n) break;
+    const float4 wh = wh4[p], wl = wl4[p];
+    float lh = 0.f, ll = 0.f;
+    if (lift) split_marked(lift[p], lh, ll);
+    const int i = p - q0;
+#pragma unroll
+    for (int cc = 0; cc < SM_COLS; ++cc) {
+      const int col = cbase + cc;
+      if (col >= B) break;
+      const float2* sc = su + cc * L;
+      const float2 c0 = sc[i], cw = sc[i - 1], ce = sc[i + 1], cs = sc[i - mx], cn = sc[i + mx];
+      float bh, bl;
+      split_marked(b[(size_t)col * n + p], bh, bl);
+      float ah = bh, al = bl;
+      if (lift) df_add(ah, al, lh, ll);
+      df_add(ah, al, -c0.x, -c0.y);
+      df_fma(ah, al, wh.x, wl.x, cw.x, cw.y);
+      df_fma(ah, al, wh.y, wl.y, ce.x, ce.y);
+      df_fma(ah, al, wh.z, wl.z, cs.x, cs.y);
+      df_fma(ah, al, wh.w, wl.w, cn.x, cn.y);
+      float s = __fadd_rn(ah, al);
+      float e = __fsub_rn(al, __fsub_rn(s, ah));
+      const float scale = fmaxf(fmaxf(fabsf(c0.x), fabsf(bh)), fabsf(lh));
+      if (!(scale >= 0x1p-60f) || !(fabsf(s) <= 3.4028234e38f))
+        split_f64_slow(residual_node_fp64(b + (size_t)col * n, u + (size_t)col * n, w4, lift,
+                                          n, mx, p), s, e);
+      store_r<RF>(R, (size_t)col * ldr + p, s, e, isc[cc]);
+      if (track) mxr[cc] = fmaxf(mxr[cc], fabsf(s));
+    }
+  }
+  if (track) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < SM_COLS; ++k) {
+      float v = mxr[k];
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) red[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < SM_COLS && cbase + (int)threadIdx.x < B) {
+      float v = 0.f;
+      for (int q = 0; q < 8; ++q) v = fmaxf(v, red[threadIdx.x][q]);
+      atomic_max_nonneg(&colmax_r[cbase + threadIdx.x], (double)v);
+    }
+  }
+}
+
+// bfloat16 of x rounded to nearest even with integer operations (binary64
+// exponent field E: 897..1150 exactly; below 2^-134 the result is a signed
+// zero); the rest through CUDA's conversion, outside the inlined code.
+__device__ __forceinline__ __nv_bfloat16 bf16_of_f64(double v) {
+  const uint64_t x = (uint64_t)__double_as_longlong(v);
+  const uint32_t hi = (uint32_t)(x >> 32);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint16_t sign = (uint16_t)((hi >> 16) & 0x8000u);
+  if (e < 889u) return __ushort_as_bfloat16(sign);
+  if (e < 897u || e > E_SPLIT_MAX) return bf16_of_f64_slow(v);
+  // 45 dropped fraction bits: above half up, exactly half to even
+  uint32_t r = ((e - 896u) << 7) | (uint32_t)((x >> 45) & 0x7Fu);
+  const uint64_t rest = x & 0x1FFFFFFFFFFFull;
+  const uint64_t half = 0x100000000000ull;
+  if (rest > half || (rest == half && (r & 1u))) r += 1u;
+  return __ushort_as_bfloat16((uint16_t)(sign | r));
+}
+
+// Prep for BF16 right-hand sides, forward mode: R = bf16(b + lift) rounded to
+// nearest (integer rounding of b alone; with a lift, from the exact pair of
+// the sticky split); optionally max |f| per column.
 __global__ void prep_df_bf16_kernel(const double* __restrict__ b, int n, int ldr,
                                     const double* __restrict__ lift,
                                     __nv_bfloat16* __restrict__ R, double* __restrict__ colmax_b,
@@ -208,20 +383,26 @@ __global__ void prep_df_bf16_kernel(const double* __restrict__ b, int n, int ldr
   float mx = 0.f;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const double bp = bc[p];
-    const double lp = lift ? lift[p] : 0.0;
-    float bh, bl, lh = 0.f, ll = 0.f, s;
     __nv_bfloat16 q;
-    if (split47<true>(bp, bh, bl) && (!lift || split47<true>(lp, lh, ll))) {
-      if (lift) df_add(bh, bl, lh, ll);
-      s = __fadd_rn(bh, bl);
-      q = bf16_of_pair(s, __fsub_rn(bl, __fsub_rn(s, bh)));
+    if (!lift) {
+      q = bf16_of_f64(bp);
     } else {
-      const double f = bp + lp;
-      s = __double2float_rn(f);
-      q = __double2bfloat16(f);
+      float bh, bl, lh, ll;
+      const double lp = lift[p];
+      const uint32_t e1 = split47<true>(bp, bh, bl), e2 = split47<true>(lp, lh, ll);
+      // both in the split's exact range (or exactly zero)
+      const bool ok = (e1 >= 920u || is_zero(bp)) && (e2 >= 920u || is_zero(lp)) &&
+                      e1 <= E_SPLIT_MAX && e2 <= E_SPLIT_MAX;
+      if (ok) {
+        df_add(bh, bl, lh, ll);
+        const float s = __fadd_rn(bh, bl);
+        q = bf16_of_pair(s, __fsub_rn(bl, __fsub_rn(s, bh)));
+      } else {
+        q = bf16_of_f64_slow(bp + lp);
+      }
     }
     R[(size_t)col * ldr + p] = q;
-    if (track) mx = fmaxf(mx, fabsf(s));
+    if (track) mx = fmaxf(mx, fabsf(__bfloat162float(q)));
   }
   if (track) {
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -244,22 +425,50 @@ pide_status launch_wsplit(pide_ctx* c, cudaStream_t st) {
   return PIDE_OK;
 }
 
+template <int NR, int COLS>
+static void launch_df_smem(pide_ctx* c, const double* b, const double* u, int B,
+                           const double* lift, int rfmt, void* R, int ldr, const float* col_scale,
+                           double* colmax_r, int t, const uint32_t* flags, size_t smem,
+                           cudaStream_t st) {
+  const dim3 g((c->n + 256 * NR - 1) / (256 * NR), (B + COLS - 1) / COLS, 1);
+  const float4* wh = c->wsp;
+  const float4* wl = c->wsp + c->n;
+  switch (rfmt) {
+    case RF_BF16: residual_df_kernel<RF_BF16, NR, COLS><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    case RF_F32: residual_df_kernel<RF_F32, NR, COLS><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    default: residual_df_kernel<RF_E4M3, NR, COLS><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+  }
+}
+
 pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, int B,
                                const double* lift, int rfmt, void* R, int ldr,
                                const float* col_scale, double* colmax_r, bool track,
                                const uint32_t* flags, cudaStream_t st) {
   if (B == 0) return PIDE_OK;
-  int gx = (c->n + 255) / 256;
-  if (gx > 1024) gx = 1024;
-  const dim3 g(gx, (B + DF_COLS - 1) / DF_COLS, 1);
-  const float4* wh = c->wsp;
-  const float4* wl = c->wsp + c->n;
+  if (rfmt != RF_BF16 && rfmt != RF_F32 && rfmt != RF_E4M3) return PIDE_EINVAL;
   const int t = track ? 1 : 0;
-  switch (rfmt) {
-    case RF_BF16: residual_df_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    case RF_F32: residual_df_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    case RF_E4M3: residual_df_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    default: return PIDE_EINVAL;
+  const int sh = c->resid_shape & 3;
+  const size_t smem = (size_t)SM_SHAPES[sh][1] * (256 * SM_SHAPES[sh][0] + 2 * (size_t)c->mx + 2) *
+                      sizeof(float2);
+  if (smem <= SMEM_MAX) {
+    switch (sh) {
+      case 1: launch_df_smem<SM_SHAPES[1][0], SM_SHAPES[1][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+      case 2: launch_df_smem<SM_SHAPES[2][0], SM_SHAPES[2][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+      case 3: launch_df_smem<SM_SHAPES[3][0], SM_SHAPES[3][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+      default: launch_df_smem<SM_SHAPES[0][0], SM_SHAPES[0][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+    }
+  } else {
+    constexpr int NR = 4, COLS = 2;
+    int gx = (c->n + 256 * NR - 1) / (256 * NR);
+    if (gx > 1024) gx = 1024;
+    const dim3 g(gx, (B + COLS - 1) / COLS, 1);
+    const float4* wh = c->wsp;
+    const float4* wl = c->wsp + c->n;
+    switch (rfmt) {
+      case RF_BF16: residual_df_reg_kernel<RF_BF16, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+      case RF_F32: residual_df_reg_kernel<RF_F32, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+      default: residual_df_reg_kernel<RF_E4M3, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    }
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;

@@ -38,12 +38,15 @@ def _bound(nx, ny, eps, f, u, r_exact):
     return 2.0 ** -23 * np.abs(r_exact) + 2.0 ** -42 * s + 2.0 ** -149
 
 
-@pytest.mark.parametrize("with_g", [False, True])
-def test_residual_df_near_solution(with_g):
+@pytest.mark.parametrize("with_g,shape", [(False, 0), (True, 0), (True, 1), (False, 2),
+                                           (True, 3)])
+def test_residual_df_near_solution(with_g, shape):
     """u close to the solution (the refinement's regime): r is ~1e-5 of u,
-    so the stencil sum cancels five orders of magnitude."""
-    nx, ny = 37, 29
-    h = 1.0 / 36
+    so the stencil sum cancels five orders of magnitude.  Every launch shape
+    of the shared-memory kernel (tiles of 1024 or 2048 nodes: several tiles
+    and a ragged last one here)."""
+    nx, ny = 77, 69
+    h = 1.0 / 76
     eps = W.eps_lognormal(nx, ny, seed=21)
     rng = np.random.default_rng(22)
     B = 7
@@ -56,6 +59,7 @@ def test_residual_df_near_solution(with_g):
     f = b + lift[None, :]
     r_exact = O.residual(nx, ny, eps, f, u)
     s = _solver(nx, ny, h, eps, "bf16")
+    s.set_tuning(resid_shape=shape)
     r = s.residual_df(b, u, g).cpu().numpy().astype(np.float64)
     bound = _bound(nx, ny, eps, f, u, r_exact)
     assert np.all(np.abs(r - r_exact) <= bound), float(np.max(np.abs(r - r_exact) / bound))
@@ -63,6 +67,25 @@ def test_residual_df_near_solution(with_g):
     if not with_g:
         r64 = s.residual(b, u).cpu().numpy()
         assert np.max(np.abs(r64 - r_exact)) <= 1e-13 * np.max(np.abs(u))
+
+
+def test_residual_df_wide_grid_register_kernel():
+    """A grid row longer than the shared-memory halo allows (1028 interior
+    nodes per row): the register kernel, with clamped neighbour loads."""
+    nx, ny = 1030, 4
+    h = 1.0 / 1029
+    eps = W.eps_lognormal(nx, ny, seed=30)
+    rng = np.random.default_rng(31)
+    n = (nx - 2) * (ny - 2)
+    u = rng.standard_normal((3, n)).cumsum(axis=1) * 1e-2
+    b = 1e-3 * rng.standard_normal((3, n))
+    g = rng.standard_normal((ny, nx))
+    f = b + O.boundary_lift(nx, ny, eps, g)[None, :]
+    r_exact = O.residual(nx, ny, eps, f, u)
+    s = _solver(nx, ny, h, eps, "bf16")
+    r = s.residual_df(b, u, g).cpu().numpy().astype(np.float64)
+    bound = _bound(nx, ny, eps, f, u, r_exact)
+    assert np.all(np.abs(r - r_exact) <= bound), float(np.max(np.abs(r - r_exact) / bound))
 
 
 def test_residual_df_special_values():
