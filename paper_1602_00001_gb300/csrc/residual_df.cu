@@ -157,9 +157,8 @@ __global__ void wsplit_kernel(const double* __restrict__ w4, int n, int mx,
 }
 
 // Launch shapes of the shared-memory kernel (PIDE_TUNE_RESID_SHAPE): SM_NR
-// nodes per thread (a tile of 256 * SM_NR nodes per block), SM_COLS columns
-// per block (the weights loaded once for all of them).
-constexpr int SM_SHAPES[4][2] = {{4, 2}, {8, 2}, {4, 1}, {8, 1}};
+// nodes per thread, a tile of 256 * SM_NR nodes per block.
+constexpr int SM_NRS[4] = {4, 8, 2, 4};
 constexpr size_t SMEM_MAX = 48 * 1024;   // larger halos (very wide grids) take the register kernel
 
 __device__ __forceinline__ int clampi(int q, int n) { return q < 0 ? 0 : (q >= n ? n - 1 : q); }
@@ -260,48 +259,73 @@ __global__ void __launch_bounds__(256, 2) residual_df_reg_kernel(
   }
 }
 
+// Packed pairs: lane x of every float2 belongs to column 2y, lane y to
+// column 2y + 1, so that one FADD2 / FMUL2 / FFMA2 instruction advances both.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void df_add2(float2& sh, float2& sl, float2 ah, float2 al) {
+  const float2 s = __fadd2_rn(sh, ah);
+  const float2 v = __fadd2_rn(s, neg2(sh));
+  const float2 e = __fadd2_rn(__fadd2_rn(sh, neg2(__fadd2_rn(s, neg2(v)))),
+                              __fadd2_rn(ah, neg2(v)));
+  sh = s;
+  sl = __fadd2_rn(sl, __fadd2_rn(al, e));
+}
+
+__device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float wh, float wl, float2 uh,
+                                        float2 ul) {
+  const float2 w = make_float2(wh, wh), v = make_float2(wl, wl);
+  const float2 ph = __fmul2_rn(w, uh);
+  float2 pl = __ffma2_rn(w, uh, neg2(ph));
+  pl = __ffma2_rn(w, ul, pl);
+  pl = __ffma2_rn(v, uh, pl);
+  df_add2(sh, sl, ph, pl);
+}
+
 // Shared-memory kernel: block (x, y) takes the tile of T = 256 * SM_NR nodes
-// from P0 = x * T and SM_COLS columns from y * SM_COLS.  It stages u over
-// [P0 - mx - 1, P0 + T + mx + 1) (the tile and one grid row of halo on each
-// side; zero outside 0..n-1) into shared memory as split float pairs, so each
-// value is split once, then thread t evaluates nodes P0 + t + 256 k: the five
-// stencil values are consecutive-per-lane shared loads (no bank conflicts).
-// The fast route needs max(|f_p|, |u_p|) >= 2^-60 and a finite result (a
-// value at or above 2^128 is staged as NaN); other nodes take the FP64 route.
-template <int RF, int SM_NR, int SM_COLS>
+// from P0 = x * T and the column pair 2y, 2y + 1.  It stages u of both
+// columns over [P0 - mx - 1, P0 + T + mx + 1) (the tile and one grid row of
+// halo on each side; zero outside 0..n-1) into shared memory as split values,
+// float4 (hi_a, hi_b, lo_a, lo_b), so each value is split once; thread t then
+// evaluates nodes P0 + t + 256 k for both columns at once: the five stencil
+// values are consecutive-per-lane shared loads.  A column past B is computed
+// on zeros and not stored.  The fast route needs max(|f_p|, |u_p|) >= 2^-60
+// and a finite result (a value at or above 2^128 is staged as NaN); other
+// nodes take the FP64 route.
+template <int RF, int SM_NR>
 __global__ void __launch_bounds__(256) residual_df_kernel(
     const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int B, int ldr,
     const float4* __restrict__ wh4, const float4* __restrict__ wl4,
     const double* __restrict__ w4, const double* __restrict__ lift, void* __restrict__ R,
     const float* __restrict__ col_scale, double* __restrict__ colmax_r, int track,
     const uint32_t* __restrict__ flags) {
-  extern __shared__ float2 su[];   // [SM_COLS][L]
-  __shared__ float red[SM_COLS][8];
+  extern __shared__ float4 su[];   // [L]
+  __shared__ float red[2][8];
   if (flags && flags[FLAG_DONE]) return;
   constexpr int T = 256 * SM_NR;
   const int L = T + 2 * mx + 2;
   const int P0 = blockIdx.x * T;
   const int q0 = P0 - mx - 1;
-  const int cbase = blockIdx.y * SM_COLS;
-#pragma unroll
-  for (int cc = 0; cc < SM_COLS; ++cc) {
-    const int col = cbase + cc;
-    if (col >= B) break;
-    const double* uc = u + (size_t)col * n;
-    for (int i = threadIdx.x; i < L; i += 256) {
-      const int q = q0 + i;
-      float h = 0.f, l = 0.f;
-      if (q >= 0 && q < n) split_marked(uc[q], h, l);
-      su[cc * L + i] = make_float2(h, l);
+  const int ca = 2 * blockIdx.y, cb = ca + 1;
+  const bool has_b = cb < B;
+  const double* ua = u + (size_t)ca * n;
+  const double* ub = u + (size_t)(has_b ? cb : ca) * n;
+  for (int i = threadIdx.x; i < L; i += 256) {
+    const int q = q0 + i;
+    float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
+    if (q >= 0 && q < n) {
+      const double va = ua[q], vb = ub[q];
+      split_marked(va, ha, la);
+      if (has_b) split_marked(vb, hb, lb);
     }
+    su[i] = make_float4(ha, hb, la, lb);
   }
   __syncthreads();
-  float isc[SM_COLS], mxr[SM_COLS];
-#pragma unroll
-  for (int cc = 0; cc < SM_COLS; ++cc) {
-    isc[cc] = (RF == RF_E4M3 && cbase + cc < B) ? 1.0f / col_scale[cbase + cc] : 1.0f;
-    mxr[cc] = 0.f;
-  }
+  const float isa = (RF == RF_E4M3) ? 1.0f / col_scale[ca] : 1.0f;
+  const float isb = (RF == RF_E4M3 && has_b) ? 1.0f / col_scale[cb] : 1.0f;
+  float mxa = 0.f, mxb = 0.f;
+  const double* ba = b + (size_t)ca * n;
+  const double* bb = b + (size_t)(has_b ? cb : ca) * n;
 #pragma unroll 2
   for (int k = 0; k < SM_NR; ++k) {
     const int p = P0 + (int)threadIdx.x + 256 * k;
@@ -309,45 +333,49 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
     const float4 wh = wh4[p], wl = wl4[p];
     float lh = 0.f, ll = 0.f;
     if (lift) split_marked(lift[p], lh, ll);
+    float bha, bla, bhb = 0.f, blb = 0.f;
+    split_marked(ba[p], bha, bla);
+    if (has_b) split_marked(bb[p], bhb, blb);
     const int i = p - q0;
-#pragma unroll
-    for (int cc = 0; cc < SM_COLS; ++cc) {
-      const int col = cbase + cc;
-      if (col >= B) break;
-      const float2* sc = su + cc * L;
-      const float2 c0 = sc[i], cw = sc[i - 1], ce = sc[i + 1], cs = sc[i - mx], cn = sc[i + mx];
-      float bh, bl;
-      split_marked(b[(size_t)col * n + p], bh, bl);
-      float ah = bh, al = bl;
-      if (lift) df_add(ah, al, lh, ll);
-      df_add(ah, al, -c0.x, -c0.y);
-      df_fma(ah, al, wh.x, wl.x, cw.x, cw.y);
-      df_fma(ah, al, wh.y, wl.y, ce.x, ce.y);
-      df_fma(ah, al, wh.z, wl.z, cs.x, cs.y);
-      df_fma(ah, al, wh.w, wl.w, cn.x, cn.y);
-      float s = __fadd_rn(ah, al);
-      float e = __fsub_rn(al, __fsub_rn(s, ah));
-      const float scale = fmaxf(fmaxf(fabsf(c0.x), fabsf(bh)), fabsf(lh));
-      if (!(scale >= 0x1p-60f) || !(fabsf(s) <= 3.4028234e38f))
-        split_f64_slow(residual_node_fp64(b + (size_t)col * n, u + (size_t)col * n, w4, lift,
-                                          n, mx, p), s, e);
-      store_r<RF>(R, (size_t)col * ldr + p, s, e, isc[cc]);
-      if (track) mxr[cc] = fmaxf(mxr[cc], fabsf(s));
+    const float4 c0 = su[i], cw = su[i - 1], ce = su[i + 1], cs = su[i - mx], cn = su[i + mx];
+    float2 ah = make_float2(bha, bhb), al = make_float2(bla, blb);
+    if (lift) df_add2(ah, al, make_float2(lh, lh), make_float2(ll, ll));
+    df_add2(ah, al, make_float2(-c0.x, -c0.y), make_float2(-c0.z, -c0.w));
+    df_fma2(ah, al, wh.x, wl.x, make_float2(cw.x, cw.y), make_float2(cw.z, cw.w));
+    df_fma2(ah, al, wh.y, wl.y, make_float2(ce.x, ce.y), make_float2(ce.z, ce.w));
+    df_fma2(ah, al, wh.z, wl.z, make_float2(cs.x, cs.y), make_float2(cs.z, cs.w));
+    df_fma2(ah, al, wh.w, wl.w, make_float2(cn.x, cn.y), make_float2(cn.z, cn.w));
+    const float2 s = __fadd2_rn(ah, al);
+    const float2 e = __fadd2_rn(al, neg2(__fadd2_rn(s, neg2(ah))));
+    float sa = s.x, ea = e.x, sb = s.y, eb = e.y;
+    if (!(fmaxf(fmaxf(fabsf(c0.x), fabsf(bha)), fabsf(lh)) >= 0x1p-60f) ||
+        !(fabsf(sa) <= 3.4028234e38f))
+      split_f64_slow(residual_node_fp64(ba, ua, w4, lift, n, mx, p), sa, ea);
+    store_r<RF>(R, (size_t)ca * ldr + p, sa, ea, isa);
+    if (track) mxa = fmaxf(mxa, fabsf(sa));
+    if (has_b) {
+      if (!(fmaxf(fmaxf(fabsf(c0.y), fabsf(bhb)), fabsf(lh)) >= 0x1p-60f) ||
+          !(fabsf(sb) <= 3.4028234e38f))
+        split_f64_slow(residual_node_fp64(bb, ub, w4, lift, n, mx, p), sb, eb);
+      store_r<RF>(R, (size_t)cb * ldr + p, sb, eb, isb);
+      if (track) mxb = fmaxf(mxb, fabsf(sb));
     }
   }
   if (track) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < SM_COLS; ++k) {
-      float v = mxr[k];
-      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) red[k][w] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      mxa = fmaxf(mxa, __shfl_xor_sync(0xffffffffu, mxa, o));
+      mxb = fmaxf(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+    }
+    if (lane == 0) {
+      red[0][w] = mxa;
+      red[1][w] = mxb;
     }
     __syncthreads();
-    if (threadIdx.x < SM_COLS && cbase + (int)threadIdx.x < B) {
+    if (threadIdx.x < 2 && (threadIdx.x == 0 || has_b)) {
       float v = 0.f;
       for (int q = 0; q < 8; ++q) v = fmaxf(v, red[threadIdx.x][q]);
-      atomic_max_nonneg(&colmax_r[cbase + threadIdx.x], (double)v);
+      atomic_max_nonneg(&colmax_r[ca + threadIdx.x], (double)v);
     }
   }
 }
@@ -425,18 +453,18 @@ pide_status launch_wsplit(pide_ctx* c, cudaStream_t st) {
   return PIDE_OK;
 }
 
-template <int NR, int COLS>
+template <int NR>
 static void launch_df_smem(pide_ctx* c, const double* b, const double* u, int B,
                            const double* lift, int rfmt, void* R, int ldr, const float* col_scale,
                            double* colmax_r, int t, const uint32_t* flags, size_t smem,
                            cudaStream_t st) {
-  const dim3 g((c->n + 256 * NR - 1) / (256 * NR), (B + COLS - 1) / COLS, 1);
+  const dim3 g((c->n + 256 * NR - 1) / (256 * NR), (B + 1) / 2, 1);
   const float4* wh = c->wsp;
   const float4* wl = c->wsp + c->n;
   switch (rfmt) {
-    case RF_BF16: residual_df_kernel<RF_BF16, NR, COLS><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    case RF_F32: residual_df_kernel<RF_F32, NR, COLS><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    default: residual_df_kernel<RF_E4M3, NR, COLS><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    case RF_BF16: residual_df_kernel<RF_BF16, NR><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    case RF_F32: residual_df_kernel<RF_F32, NR><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    default: residual_df_kernel<RF_E4M3, NR><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
   }
 }
 
@@ -447,15 +475,13 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   if (B == 0) return PIDE_OK;
   if (rfmt != RF_BF16 && rfmt != RF_F32 && rfmt != RF_E4M3) return PIDE_EINVAL;
   const int t = track ? 1 : 0;
-  const int sh = c->resid_shape & 3;
-  const size_t smem = (size_t)SM_SHAPES[sh][1] * (256 * SM_SHAPES[sh][0] + 2 * (size_t)c->mx + 2) *
-                      sizeof(float2);
+  const int nr = SM_NRS[c->resid_shape & 3];
+  const size_t smem = (256 * (size_t)nr + 2 * (size_t)c->mx + 2) * sizeof(float4);
   if (smem <= SMEM_MAX) {
-    switch (sh) {
-      case 1: launch_df_smem<SM_SHAPES[1][0], SM_SHAPES[1][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
-      case 2: launch_df_smem<SM_SHAPES[2][0], SM_SHAPES[2][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
-      case 3: launch_df_smem<SM_SHAPES[3][0], SM_SHAPES[3][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
-      default: launch_df_smem<SM_SHAPES[0][0], SM_SHAPES[0][1]>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+    switch (nr) {
+      case 8: launch_df_smem<8>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+      case 2: launch_df_smem<2>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+      default: launch_df_smem<4>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
     }
   } else {
     constexpr int NR = 4, COLS = 2;
