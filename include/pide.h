@@ -279,8 +279,9 @@ pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
  *                           0 < tol < 1e-8, where only the FP64 stencil resolves the residual.
  *                           0: the FP64 stencil always.  pide_residual and the rel_residual
  *                           of pide_info are always FP64.
- *   PIDE_TUNE_RESID_SHAPE   launch shape of that residual kernel, consecutive nodes x columns
- *                           per thread: 0 (default) 4 x 2, 1: 4 x 1, 2: 2 x 2, 3: 2 x 1 */
+ *   PIDE_TUNE_RESID_SHAPE   launch shape of that residual kernel: nodes per thread (a tile of
+ *                           256 x that many nodes per block, two columns per block):
+ *                           0: 4, 1 (default): 8, 2: 2, 3: 4 */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
