@@ -150,6 +150,23 @@ pide_status pide_apply_host(pide_handle h, const double* b_host, double* u_host,
                             int32_t max_sweeps, double tol, void* stream, pide_info* info);
 
 /*
+ * pide_solve_stream -- a time sequence of T right-hand sides (Eq. 1 with a
+ * time-dependent charge, one solve per time step) from HOST memory:
+ * in_host[T][n] float64 holds b (charge = 0) or the charge density rho
+ * (charge = 1: b = -h^2 rho / d on the device, as pide_rhs_from_charge), and
+ * u_host[T][n] receives the solutions.  The columns go through two device
+ * slots of `chunk` columns (chunk in [1, 65535]; allocated by the handle on
+ * first use, 4 * chunk * n * 8 bytes, kept for later calls): the copy of
+ * chunk i + 1 to the device and of chunk i - 1 to the host run on internal
+ * streams under the refined solve of chunk i (max_sweeps refinement sweeps,
+ * fixed count).  Pinned host memory is needed for the copies to overlap.
+ * Ordered after the work already on `stream`; returns after synchronising.
+ * in_host and u_host must not overlap.
+ */
+pide_status pide_solve_stream(pide_handle h, const double* in_host, double* u_host, int64_t T,
+                              int32_t chunk, int32_t max_sweeps, int32_t charge, void* stream);
+
+/*
  * pide_residual -- r = b - L u at interior nodes (Eq. 3 as a matrix-free
  * 5-point stencil, FP64, zero boundary values).  b, u, r are [B][n]; r may
  * alias neither b nor u.

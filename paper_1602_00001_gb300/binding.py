@@ -75,6 +75,7 @@ _SIGS = {
     "pide_selftest_wait_timeout": (_I, [ctypes.c_int64, _P]),
     "pide_selftest_convert": (_I, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "pide_selftest_residual_df": (_I, [_P, _P, _P, _P, _P, _I, _P]),
+    "pide_solve_stream": (_I, [_P, _P, _P, ctypes.c_int64, _I, _I, _I, _P]),
     "pide_status_string": (ctypes.c_char_p, [_I]),
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),
@@ -208,6 +209,28 @@ class Solver:
                                         ctypes.byref(info) if want_info else None),
                "pide_apply_host")
         return (u_host, info) if want_info else u_host
+
+    def solve_stream(self, in_host, u_host=None, chunk: int = 1024, sweeps: int = 0,
+                     charge: bool = False, stream=None):
+        """pide_solve_stream: T right-hand sides (or charge densities) in host
+        memory, [T][n] float64 (numpy or pinned torch CPU tensor), solved in
+        chunks with the copies overlapping the solves; returns u on the host."""
+        import torch
+        if isinstance(in_host, torch.Tensor):
+            T = in_host.reshape(-1, self.n).shape[0]
+            if u_host is None:
+                u_host = torch.empty_like(in_host)
+            iptr, uptr = in_host.data_ptr(), u_host.data_ptr()
+        else:
+            in_host = np.ascontiguousarray(in_host, dtype=np.float64).reshape(-1, self.n)
+            T = in_host.shape[0]
+            if u_host is None:
+                u_host = np.empty_like(in_host)
+            iptr, uptr = in_host.ctypes.data, u_host.ctypes.data
+        _check(self.lib.pide_solve_stream(self.handle, ctypes.c_void_p(iptr), ctypes.c_void_p(uptr),
+                                          T, int(chunk), int(sweeps), 1 if charge else 0,
+                                          _stream(stream)), "pide_solve_stream")
+        return u_host
 
     def residual(self, b, u, stream=None):
         import torch

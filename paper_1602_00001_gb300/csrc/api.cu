@@ -336,6 +336,8 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   for (int k = 0; k < 6; ++k) PIDE_CUDA_TRY(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
   PIDE_CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
   for (int k = 0; k < 6; ++k) PIDE_CUDA_TRY(cudaEventCreateWithFlags(&c->hev[k], cudaEventDisableTiming));
+  PIDE_CUDA_TRY(cudaStreamCreateWithFlags(&c->dstream, cudaStreamNonBlocking));
+  for (int k = 0; k < 9; ++k) PIDE_CUDA_TRY(cudaEventCreateWithFlags(&c->sev[k], cudaEventDisableTiming));
   PIDE_CUDA_TRY(cudaMemcpyAsync(c->eps, c->eps_host.data(), N * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
   PIDE_TRY(launch_assemble(c, st));
@@ -418,7 +420,7 @@ extern "C" void pide_destroy(pide_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {h->sym, h->sym_lo, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
-                  h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u};
+                  h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : h->prof_events) {
@@ -429,8 +431,11 @@ extern "C" void pide_destroy(pide_handle h) {
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->hev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->sev)
+    if (e) cudaEventDestroy(e);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->cstream) cudaStreamDestroy(h->cstream);
+  if (h->dstream) cudaStreamDestroy(h->dstream);
   delete h;
 }
 
@@ -514,6 +519,70 @@ extern "C" pide_status pide_apply_host(pide_handle h, const double* b_host, doub
   PIDE_TRY(solve_s(h, h->hbuf_b, 0, nullptr, h->hbuf_u, B, max_sweeps, tol, st));
   PIDE_CUDA_TRY(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, st));
   if (info) return fill_info(h, h->hbuf_b, h->hbuf_u, B, 0, nullptr, max_sweeps, tol, st, info);
+  return check_device_error(h, st);
+}
+
+// Eq. (1) with time: a sequence of right-hand sides (or charge densities) in
+// host memory solved chunk by chunk.  Slot q = i & 1 of the two device slots
+// holds chunk i; its input copy (cstream) waits until chunk i - 2 has been
+// solved, its solve (st) waits for that copy and for the output copy of
+// chunk i - 2 (dstream), and its output copy waits for the solve, so chunk
+// i's solve runs under chunk i + 1's input copy and chunk i - 1's output copy.
+extern "C" pide_status pide_solve_stream(pide_handle h, const double* in_host, double* u_host,
+                                         int64_t T, int32_t chunk, int32_t sweeps,
+                                         int32_t charge, void* stream) {
+  if (!h || T < 0 || chunk < 1 || chunk > 65535 || sweeps < 0 || (T > 0 && (!in_host || !u_host)) ||
+      (const void*)in_host == (const void*)u_host) {
+    set_error("pide_solve_stream: bad argument (handle, pointers, T >= 0, chunk in [1, 65535], "
+              "sweeps >= 0, in != u)");
+    return PIDE_EINVAL;
+  }
+  if (T == 0) return PIDE_OK;
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int cols = (int)(T < chunk ? T : chunk);
+  if (cols > h->sbuf_cols) {
+    if (h->sbuf_in) cudaFree(h->sbuf_in);
+    if (h->sbuf_out) cudaFree(h->sbuf_out);
+    h->sbuf_in = h->sbuf_out = nullptr;
+    h->sbuf_cols = 0;
+    PIDE_CUDA_TRY(cudaMalloc((void**)&h->sbuf_in, 2 * (size_t)cols * h->n * sizeof(double)));
+    PIDE_CUDA_TRY(cudaMalloc((void**)&h->sbuf_out, 2 * (size_t)cols * h->n * sizeof(double)));
+    h->sbuf_cols = cols;
+  }
+  PIDE_TRY(ensure_workspace(h, cols));
+  const size_t slot = (size_t)cols * h->n;
+  cudaEvent_t fork = h->sev[0], copied_in[2] = {h->sev[1], h->sev[2]},
+              solved[2] = {h->sev[3], h->sev[4]}, copied_out[2] = {h->sev[5], h->sev[6]},
+              end_in = h->sev[7], end_out = h->sev[8];
+  // the copy streams start after the work already queued on st
+  PIDE_CUDA_TRY(cudaEventRecord(fork, st));
+  PIDE_CUDA_TRY(cudaStreamWaitEvent(h->cstream, fork, 0));
+  PIDE_CUDA_TRY(cudaStreamWaitEvent(h->dstream, fork, 0));
+  const int64_t nchunks = (T + cols - 1) / cols;
+  for (int64_t i = 0; i < nchunks; ++i) {
+    const int q = (int)(i & 1);
+    const int64_t c0 = i * cols;
+    const int nc = (int)((T - c0) < cols ? (T - c0) : cols);
+    const size_t off = (size_t)c0 * h->n, bytes = (size_t)nc * h->n * sizeof(double);
+    double* din = h->sbuf_in + q * slot;
+    double* dout = h->sbuf_out + q * slot;
+    if (i >= 2) PIDE_CUDA_TRY(cudaStreamWaitEvent(h->cstream, solved[q], 0));
+    PIDE_CUDA_TRY(cudaMemcpyAsync(din, in_host + off, bytes, cudaMemcpyHostToDevice, h->cstream));
+    PIDE_CUDA_TRY(cudaEventRecord(copied_in[q], h->cstream));
+    PIDE_CUDA_TRY(cudaStreamWaitEvent(st, copied_in[q], 0));
+    if (i >= 2) PIDE_CUDA_TRY(cudaStreamWaitEvent(st, copied_out[q], 0));
+    if (charge) PIDE_TRY(launch_rhs_from_charge(h, din, din, nc, st));
+    PIDE_TRY(solve_s(h, din, 0, nullptr, dout, nc, sweeps, 0.0, st));
+    PIDE_CUDA_TRY(cudaEventRecord(solved[q], st));
+    PIDE_CUDA_TRY(cudaStreamWaitEvent(h->dstream, solved[q], 0));
+    PIDE_CUDA_TRY(cudaMemcpyAsync(u_host + off, dout, bytes, cudaMemcpyDeviceToHost, h->dstream));
+    PIDE_CUDA_TRY(cudaEventRecord(copied_out[q], h->dstream));
+  }
+  PIDE_CUDA_TRY(cudaEventRecord(end_in, h->cstream));
+  PIDE_CUDA_TRY(cudaEventRecord(end_out, h->dstream));
+  PIDE_CUDA_TRY(cudaStreamWaitEvent(st, end_in, 0));
+  PIDE_CUDA_TRY(cudaStreamWaitEvent(st, end_out, 0));
   return check_device_error(h, st);
 }
 

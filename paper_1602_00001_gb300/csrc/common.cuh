@@ -99,6 +99,13 @@ struct pide_ctx {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t cstream = nullptr;   // host<->device copies of pide_apply_host
   cudaEvent_t hev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // pide_solve_stream: two device slots of `sbuf_cols` columns for the input and
+  // the solution, copies in on cstream and out on dstream
+  cudaStream_t dstream = nullptr;
+  cudaEvent_t sev[9] = {};
+  double* sbuf_in = nullptr;
+  double* sbuf_out = nullptr;
+  int sbuf_cols = 0;
   int gemv_max_b = 1;               // largest B sent to the GEMV kernel (tcgen05 above)
   int gemv_threads = 1024;          // GEMV block size (multiple of 32, <= 1024)
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8
