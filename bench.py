@@ -308,6 +308,91 @@ def adjoint_workload(args):
     return 0
 
 
+def formats_workload(args):
+    """Table 1 on the GPU and its extension to the binary stored formats.
+
+    (a) The Eq. (4)/(5) problem on n x n nodes, n in {5, 11, 21, 41, 81}: the
+    FP64 inverse formed on the GPU, rounded to k decimals on the GPU, one FP64
+    apply, Eq. (6) error; beside the printed value.  (b) For FP32, BF16, FP8 and
+    FP8 hi+lo stores, Fourier-field eps, 16 right-hand sides: Eq. (6) error
+    against the FP64 GPU apply after k refinement sweeps, the contraction per
+    sweep and the sweeps needed for 1e-6, on grids from 21^2 to 200^2 nodes."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import pide_oracle as O
+    from paper_1602_00001_gb300 import workloads as W
+    from paper_1602_00001_gb300.binding import Solver
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    golden = os.path.join(ROOT, "tests", "golden", "table1.txt")
+    printed = {}
+    for ln in open(golden):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        parts = ln.split()
+        for n, v in zip([5, 11, 21, 41, 81], parts[1:]):
+            printed[(n, parts[0])] = v
+    table, match = {}, 0
+    t0 = time.perf_counter()
+    for n in [5, 11, 21, 41, 81]:
+        h = 1.0 / (n - 1)
+        x = h * np.arange(n)
+        X, Y = np.meshgrid(x, x)
+        f = O.eq4_source(X, Y)[1:-1, 1:-1].reshape(1, -1)
+        ua = O.eq5_exact(X, Y)
+        for k in ["1", "2", "3", "5", "none"]:
+            s = Solver(n, n, h, np.ones((n, n)), "fp64")
+            b = s.rhs_from_charge(f)
+            if k != "none":
+                s.round_inverse_decimal(int(k))
+            u = np.zeros((n, n))
+            u[1:-1, 1:-1] = s.apply(b).cpu().numpy().reshape(n - 2, n - 2)
+            err = float(np.max(np.abs(ua - u)) / np.max(np.abs(ua)))
+            p = printed[(n, k)]
+            ok = abs(err - float(p)) <= 0.5 * 10.0 ** (-len(p.split(".")[1])) + 1e-12
+            match += int(ok)
+            table[f"n={n},digits={k}"] = {"gpu": err, "printed": float(p), "match": ok}
+            s.close()
+    t_table = time.perf_counter() - t0
+    study = {}
+    B = 16
+    for N in [21, 41, 81, 161, 200]:
+        h = 1.0 / (N - 1)
+        eps = W.eps_fourier(N, N, h, seed=1)
+        rho = W.moving_charges(N, N, h, seed=5, steps=B)
+        s64 = Solver(N, N, h, eps, "fp64")
+        b = s64.rhs_from_charge(torch.from_numpy(rho).cuda())
+        ref = s64.apply(b)
+        s64.close()
+        row = {}
+        for prec in ["fp32", "bf16", "fp8", "fp8x2"]:
+            s = Solver(N, N, h, eps, prec)
+            errs = []
+            for k in range(0, 9):
+                u = s.apply(b, sweeps=k)
+                errs.append(float(((u - ref).abs().amax(dim=1) / ref.abs().amax(dim=1)).max()))
+                if errs[-1] < 1e-13:
+                    break
+            ratios = [errs[i + 1] / errs[i] for i in range(len(errs) - 1) if errs[i + 1] > 1e-12]
+            need = next((k for k, e in enumerate(errs) if e <= 1e-6), None)
+            row[prec] = {"err_by_sweeps": errs, "store_bytes": s.info().store_bytes,
+                         "contraction": float(np.median(ratios)) if ratios else None,
+                         "sweeps_for_1e-6": need}
+            s.close()
+        study[f"{N}x{N}"] = row
+    line = {"metric": "Table 1 cells reproduced on the GPU (of 25)", "value": match,
+            "unit": "cells", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_table * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "Table 1 (Eq. 4/5, n = 5..81, digits 1, 2, 3, 5, none) and "
+                                   "stored-format study (Fourier eps, 16 moving charges, "
+                                   "21^2..200^2 nodes)"},
+            "table1": table, "formats": study}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,8 +404,9 @@ def main():
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--nodes", type=int, default=NODES, help="grid nodes per side (profiling runs)")
-    ap.add_argument("--workload", default="apply", choices=["apply", "batched", "adjoint"],
-                    help="apply: the headline (default); batched / adjoint: the other rows")
+    ap.add_argument("--workload", default="apply",
+                    choices=["apply", "batched", "adjoint", "formats"],
+                    help="apply: the headline (default); batched / adjoint / formats: other rows")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -328,6 +414,8 @@ def main():
         return batched_workload(args)
     if args.workload == "adjoint":
         return adjoint_workload(args)
+    if args.workload == "formats":
+        return formats_workload(args)
 
     import numpy as np
     import torch

@@ -268,6 +268,14 @@ pide_status pide_profile_end(pide_handle h, pide_profile* out);
  * applied) to host memory dst[n]: lets tests check individual entries. */
 pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
 
+/* Table 1's experiment: round every entry of the stored inverse of an FP64
+ * handle to `digits` digits after the decimal point, in place, half away from
+ * zero, x -> sign(x) floor(|x| 10^digits + 1/2) / 10^digits with each FP64
+ * operation rounded separately (digits in [0, 15]).  Later applies of the
+ * handle use the rounded inverse.  FP64 handles only (PIDE_EUNSUPPORTED
+ * otherwise).  Stream-ordered. */
+pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stream);
+
 /* Launch-shape knobs of the apply kernels (set by the autotuner; results do
  * not depend on them beyond FP32 summation order).
  *   PIDE_TUNE_GEMV_THREADS  GEMV block size: 128..1024, multiple of 32 (default 1024)

@@ -76,6 +76,7 @@ _SIGS = {
     "pide_selftest_convert": (_I, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "pide_selftest_residual_df": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "pide_solve_stream": (_I, [_P, _P, _P, ctypes.c_int64, _I, _I, _I, _P]),
+    "pide_round_inverse_decimal": (_I, [_P, _I, _P]),
     "pide_status_string": (ctypes.c_char_p, [_I]),
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),
@@ -296,6 +297,11 @@ class Solver:
 
     def reserve(self, Bmax: int):
         _check(self.lib.pide_reserve(self.handle, int(Bmax)), "pide_reserve")
+
+    def round_inverse_decimal(self, digits: int, stream=None):
+        """Table 1: round the stored FP64 inverse to `digits` decimals, in place."""
+        _check(self.lib.pide_round_inverse_decimal(self.handle, int(digits), _stream(stream)),
+               "pide_round_inverse_decimal")
 
     def inverse_row(self, p: int) -> np.ndarray:
         out = np.empty(self.n, dtype=np.float64)

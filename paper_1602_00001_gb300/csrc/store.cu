@@ -81,6 +81,19 @@ __global__ void row_to_f64_kernel(const void* __restrict__ inv, const void* __re
   }
 }
 
+// Table 1's rounding of the inverse: x -> sign(x) floor(|x| 10^k + 1/2) / 10^k,
+// each operation rounded separately in FP64 (no FMA contraction), so that the
+// same input gives the same decimal as a plain FP64 evaluation of the formula.
+__global__ void round_decimal_kernel(double* __restrict__ G, size_t ld, int n, double scale) {
+  const size_t total = (size_t)n * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double x = G[e];
+    const double m = floor(__dadd_rn(__dmul_rn(fabs(x), scale), 0.5));
+    G[e] = copysign(__ddiv_rn(m, scale), x);
+  }
+}
+
 }  // namespace
 
 pide_status quantize_store(pide_ctx* c, const double* G, cudaStream_t st) {
@@ -129,5 +142,24 @@ extern "C" pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* ds
   cudaError_t e = cudaMemcpy(dst_host, tmp, h->n * sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(tmp);
   PIDE_CUDA_TRY(e);
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stream) {
+  using namespace pide;
+  if (!h || digits < 0 || digits > 15) {
+    set_error("pide_round_inverse_decimal: bad argument (digits in [0, 15])");
+    return PIDE_EINVAL;
+  }
+  if (h->prec != PIDE_FP64) {
+    set_error("pide_round_inverse_decimal: FP64 handles only");
+    return PIDE_EUNSUPPORTED;
+  }
+  PIDE_CUDA_TRY(cudaSetDevice(h->device));
+  double scale = 1.0;
+  for (int k = 0; k < digits; ++k) scale *= 10.0;   // exact for digits <= 15
+  round_decimal_kernel<<<h->num_sms * 8, 256, 0, (cudaStream_t)stream>>>((double*)h->inv,
+                                                                         (size_t)h->ld, h->n, scale);
+  PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
