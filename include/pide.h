@@ -306,7 +306,10 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           of pide_info are always FP64.
  *   PIDE_TUNE_RESID_SHAPE   launch shape of that residual kernel: nodes per thread (a tile of
  *                           256 x that many nodes per block, two columns per block):
- *                           0: 4, 1 (default): 8, 2: 2, 3: 4 */
+ *                           0: 4, 1 (default): 8, 2: 2, 3: 4
+ *   PIDE_TUNE_GEMM_2CTA     1: for B > 128 (with GEMM_BN 256) the tensor-core apply runs on pairs
+ *                           of SMs (tcgen05 cta_group::2, 256 x 256 tiles, each SM staging half
+ *                           of each operand tile); 0 (default): one SM per 128 x 256 tile */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -317,7 +320,8 @@ typedef enum {
   PIDE_TUNE_RESID_CTAS = 6,
   PIDE_TUNE_SYMV = 7,
   PIDE_TUNE_RESID_EMUL = 8,
-  PIDE_TUNE_RESID_SHAPE = 9
+  PIDE_TUNE_RESID_SHAPE = 9,
+  PIDE_TUNE_GEMM_2CTA = 10
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -93,6 +93,8 @@ struct pide_ctx {
   // launch-shape knobs (pide_set_tuning; the autotuner sets them)
   int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
   int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
+  int gemm_2cta = 0;                // B > 128 on SM pairs (tcgen05 cta_group::2)
+  int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
   int overlap = 0;                  // residual of one column group under the GEMM of the other
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
   cudaStream_t aux = nullptr;       // low-priority stream for the overlapped residuals
@@ -174,6 +176,9 @@ int rhs_format(const pide_ctx* c, int B);   // element format R must hold for th
 // tensor-core GEMM (BF16, FP8X2) and SIMT paths
 pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
                            int col0 = 0);
+// the same on pairs of SMs (tcgen05 cta_group::2, 256 x 256 tiles), for B > 128
+pide_status launch_gemm_tc2(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                            int col0 = 0);
 pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 pide_status build_sym_store(pide_ctx* c, const double* G, cudaStream_t st);   // G = L^-1 (FP64)
 pide_status launch_symv(pide_ctx* c, double* u, bool accumulate, cudaStream_t st);

@@ -386,8 +386,18 @@ pide_status launch_tc_mode(pide_ctx* c, int B, double* u, bool accumulate, cudaS
 
 }  // namespace
 
+pide_status launch_zero_tiles(pide_ctx* c, double* u, int B, int bm, int bn, int n_tiles,
+                              int first_tile, int count, cudaStream_t st) {
+  if (count <= 0) return PIDE_OK;
+  zero_tiles_kernel<<<count, 256, 0, st>>>(u, c->n, B, bm, bn, n_tiles, first_tile, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
 pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
                            int col0) {
+  if (c->gemm_2cta && B > 128 && c->gemm_bn_large == 256)
+    return launch_gemm_tc2(c, B, u, accumulate, st, col0);
   if (!c->tmA_ok) {
     set_error("tensor-core apply: TMA maps were not created");
     return PIDE_EUNSUPPORTED;
