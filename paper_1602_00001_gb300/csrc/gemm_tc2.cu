@@ -33,7 +33,7 @@ constexpr int BM2 = 256;          // output rows per cluster tile (128 per CTA)
 constexpr int BN2 = 256;          // right-hand sides per cluster tile (128 staged per CTA)
 constexpr int HALF = 128;
 constexpr int ROW_BYTES2 = 128;   // one 128-byte swizzle row of K per stage
-constexpr int TC2_NACC = 1;       // accumulators per pair
+constexpr int TC2_NACC = 2;       // accumulators per pair (512 TMEM columns)
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
