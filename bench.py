@@ -404,6 +404,8 @@ def main():
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--nodes", type=int, default=NODES, help="grid nodes per side (profiling runs)")
+    ap.add_argument("--tune", action="append", default=[], metavar="KEY=VALUE",
+                    help="launch-shape knob of the refined solver (pide_set_tuning), repeatable")
     ap.add_argument("--workload", default="apply",
                     choices=["apply", "batched", "adjoint", "formats"],
                     help="apply: the headline (default); batched / adjoint / formats: other rows")
@@ -471,6 +473,9 @@ def main():
 
     # ---- the refined low-precision solver
     s = Solver(NN, NN, h, eps, args.precision)
+    tune = dict(kv.split("=", 1) for kv in args.tune)
+    if tune:
+        s.set_tuning(**{k: int(v) for k, v in tune.items()})
     s.reserve(B)
     n = s.n
     u = torch.empty((B, n), dtype=torch.float64, device="cuda")
@@ -616,12 +621,15 @@ def main():
                      "speedup_b1_vs_fp64": fp64_b1_ms / b1_ms},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": traffic,
-                     "kernel": f"gemm_tc_kernel (tcgen05 {args.precision}, M=128 N=256)",
+                     "kernel": (f"gemm_tc2_kernel (tcgen05 cta_group::2 {args.precision}, M=256 N=256 per SM pair)"
+                                if s.get_tuning()["gemm_2cta"] and B > 128 else
+                                f"gemm_tc_kernel (tcgen05 {args.precision}, M=128 N=256)"),
                      "peak_source": peak_src,
                      "avg_launch_ms": gemm_ms, "launches": apply_launches,
                      "algorithmic_flops_per_launch": flops_total / max(apply_launches, 1)},
         "kernel_ms_per_step": {c: prof[c][1] / args.steps for c in prof},
         "overlap": bool(s.get_tuning()["overlap"]),
+        "tuning": s.get_tuning(),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * 8,
                 "d2h_bytes_per_step": B * n * 8,
