@@ -77,6 +77,8 @@ def test_pair_refined_equals_single_sm():
     eps = W.eps_lognormal(nx, ny, seed=12)
     b = _b(nx, ny, h, eps, 640, seed=13)
     s = _solver(nx, ny, h, eps, "bf16")
+    assert s.get_tuning()["gemm_2cta"] == 1           # the default
+    s.set_tuning(gemm_2cta=0)
     u1 = s.apply(b, sweeps=4).cpu().numpy()
     s.set_tuning(gemm_2cta=1)
     u2 = s.apply(b, sweeps=4).cpu().numpy()
@@ -94,6 +96,7 @@ def test_pair_full_size_sampled():
     rho = W.moving_charges(nx, ny, h, seed=5, steps=1024)
     s = _solver(nx, ny, h, eps, "bf16")
     b = s.rhs_from_charge(torch.from_numpy(rho).cuda())
+    s.set_tuning(gemm_2cta=0)
     u1 = s.apply(b, sweeps=4)
     s.set_tuning(gemm_2cta=1)
     u2 = s.apply(b, sweeps=4)

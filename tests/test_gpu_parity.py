@@ -129,13 +129,14 @@ def test_bf16_single_apply_is_exact_contraction(B):
     b = _b(nx, ny, h, eps, B, seed=B)
     s = _solver(nx, ny, h, eps, "bf16")
     s.set_tuning(symv=0)          # B = 1 through the full stored L^-1 here
-    for limit in ([1, 8] if B <= 8 else [1]):
-        s.set_tuning(gemv_max_b=limit)
+    # B > 128: the SM-pair kernel (default) and the single-SM kernel
+    for limit, pair in ([(1, 1), (8, 1)] if B <= 8 else [(1, 1), (1, 0)] if B > 128 else [(1, 1)]):
+        s.set_tuning(gemv_max_b=limit, gemm_2cta=pair)
         u = s.apply(b, sweeps=0).cpu().numpy()
         rhs_round = O.round_fp32 if B <= limit else O.round_bf16
         ref, mag = _oracle_lowprec_apply(nx, ny, eps, b, O.round_bf16, rhs_round)
         err = np.abs(u - ref)
-        assert np.all(err <= 2e-5 * mag + 1e-300), (limit, float(np.max(err / mag)))
+        assert np.all(err <= 2e-5 * mag + 1e-300), (limit, pair, float(np.max(err / mag)))
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
