@@ -309,7 +309,9 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           0: 4, 1 (default): 8, 2: 2, 3: 4
  *   PIDE_TUNE_GEMM_2CTA     1 (default): for B > 128 (with GEMM_BN 256) the tensor-core apply runs
  *                           on pairs of SMs (tcgen05 cta_group::2, 256 x 256 tiles, each SM
- *                           staging half of each operand tile); 0: one SM per 128 x 256 tile */
+ *                           staging half of each operand tile); 0: one SM per 128 x 256 tile
+ *   PIDE_TUNE_GEMM_A_HINT   L2 policy of the tensor-core apply's loads of the stored inverse:
+ *                           0 (default) evict-first, 1 evict-normal, 2 evict-last */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -321,7 +323,8 @@ typedef enum {
   PIDE_TUNE_SYMV = 7,
   PIDE_TUNE_RESID_EMUL = 8,
   PIDE_TUNE_RESID_SHAPE = 9,
-  PIDE_TUNE_GEMM_2CTA = 10
+  PIDE_TUNE_GEMM_2CTA = 10,
+  PIDE_TUNE_GEMM_A_HINT = 11
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

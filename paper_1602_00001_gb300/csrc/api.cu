@@ -898,6 +898,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 0 && value != 1) break;
       h->gemm_2cta = value;
       return PIDE_OK;
+    case PIDE_TUNE_GEMM_A_HINT:
+      if (value < 0 || value > 2) break;
+      h->gemm_a_hint = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -920,6 +924,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_RESID_EMUL: *value = h->resid_emul; return PIDE_OK;
     case PIDE_TUNE_RESID_SHAPE: *value = h->resid_shape; return PIDE_OK;
     case PIDE_TUNE_GEMM_2CTA: *value = h->gemm_2cta; return PIDE_OK;
+    case PIDE_TUNE_GEMM_A_HINT: *value = h->gemm_a_hint; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

@@ -94,6 +94,7 @@ struct pide_ctx {
   int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
   int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
   int gemm_2cta = 1;                // B > 128 on SM pairs (tcgen05 cta_group::2)
+  int gemm_a_hint = 0;              // L2 policy of the inverse's TMA loads (policy_for_a)
   int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
   int overlap = 0;                  // residual of one column group under the GEMM of the other
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
@@ -295,6 +296,17 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// L2 policy for the streamed inverse: 0 evict-first, 1 evict-normal, 2 evict-last
+__device__ __forceinline__ uint64_t policy_for_a(int hint) {
+  return hint == 0 ? policy_evict_first() : (hint == 1 ? policy_evict_normal() : policy_evict_last());
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {

@@ -104,7 +104,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-               uint32_t* __restrict__ flags) {
+               uint32_t* __restrict__ flags, int a_hint) {
   constexpr bool FP8 = MODE != 0;
   constexpr bool LO = MODE == 2;
   using C = TcCfg<BN, FP8>;
@@ -156,7 +156,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer
-    const uint64_t pol_a = policy_evict_first();   // the inverse streams through L2 once
+    const uint64_t pol_a = policy_for_a(a_hint);    // the inverse streams through L2 once
     const uint64_t pol_r = policy_evict_last();    // the right-hand sides are re-read by every slab
     int s = 0;
     uint32_t ph = 0;
@@ -357,7 +357,7 @@ pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream
   }
   kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, col0, num_kb, dp_tiles, sk,
                                 u, accumulate ? 1 : 0, c->row_scale,
-                                MODE != 0 ? c->col_scale + col0 : nullptr, c->flags);
+                                MODE != 0 ? c->col_scale + col0 : nullptr, c->flags, c->gemm_a_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }

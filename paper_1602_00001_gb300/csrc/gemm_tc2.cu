@@ -174,7 +174,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                 int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                 const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-                uint32_t* __restrict__ flags) {
+                uint32_t* __restrict__ flags, int a_hint) {
   constexpr bool FP8 = MODE != 0;
   constexpr bool LO = MODE == 2;
   constexpr int A_BYTES = HALF * ROW_BYTES2;                  // 16 KB
@@ -235,7 +235,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer (both CTAs)
-    const uint64_t pol_a = policy_evict_first();
+    const uint64_t pol_a = policy_for_a(a_hint);
     const uint64_t pol_r = policy_evict_last();
     int s = 0;
     uint32_t ph = 0;
@@ -435,7 +435,7 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
     PIDE_TRY(launch_zero_tiles(c, u, B, BM2, BN2, n_tiles, dp_tiles, tiles - dp_tiles, st));
   kern<<<2 * clusters, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, col0, num_kb, dp_tiles,
                                         sk, u, accumulate ? 1 : 0, c->row_scale,
-                                        MODE != 0 ? c->col_scale + col0 : nullptr, c->flags);
+                                        MODE != 0 ? c->col_scale + col0 : nullptr, c->flags, c->gemm_a_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
