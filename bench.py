@@ -34,17 +34,16 @@ TARGET_ERR = 0.5e-6          # calibration target (the bar is 1e-6)
 WORKLOAD = "198^2 interior (200x200 nodes), Fourier-field eps, 16 moving charges, B=1024"
 
 
-# DRAM traffic of one refinement launch of the GEMM at this workload, from the ncu
-# capture summarised in profiles/gemm_tc_bf16_198sq_b1024.md; valid only for the
-# kernel source it was taken on (sha1 of csrc/gemm_tc.cu + csrc/common.cuh).
-GEMM_TRAFFIC = {"sha1": "dc333af6f97de5099ba214700d99de25603f442e", "bytes": 4.50e9 + 0.328e9,
-                "precision": "bf16", "batch": 1024, "nodes": 200}
+# DRAM traffic (read + write) of one launch of the GEMM at this workload, from the
+# one-pass ncu capture summarised in profiles/gemm_tc2_bf16_198sq_b1024.md; valid
+# only for the kernel source it was taken on (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh).
+GEMM_TRAFFIC = {"sha1": None, "bytes": None, "precision": "bf16", "batch": 1024, "nodes": 200}
 
 
 def gemm_source_sha1():
     import hashlib
     h = hashlib.sha1()
-    for f in ("gemm_tc.cu", "common.cuh"):
+    for f in ("gemm_tc2.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1602_00001_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -593,8 +592,10 @@ def main():
         peak_tf = pk["bf16_tflops_sustained"]
         peak_src = f"{pk_kind} bf16_tflops_sustained"
     traffic = None
+    tn = s.get_tuning()
     if (gemm_source_sha1() == GEMM_TRAFFIC["sha1"] and args.precision == GEMM_TRAFFIC["precision"]
-            and B == GEMM_TRAFFIC["batch"] and NN == GEMM_TRAFFIC["nodes"]):
+            and B == GEMM_TRAFFIC["batch"] and NN == GEMM_TRAFFIC["nodes"]
+            and tn["gemm_2cta"] == 1 and tn["gemm_a_hint"] == 1):
         traffic = GEMM_TRAFFIC["bytes"]
     launches = sum(prof[c][0] for c in prof)
 
