@@ -261,25 +261,42 @@ __global__ void __launch_bounds__(256, 2) residual_df_reg_kernel(
 
 // Packed pairs: lane x of every float2 belongs to column 2y, lane y to
 // column 2y + 1, so that one FADD2 / FMUL2 / FFMA2 instruction advances both.
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-
-__device__ __forceinline__ void df_add2(float2& sh, float2& sl, float2 ah, float2 al) {
-  const float2 s = __fadd2_rn(sh, ah);
-  const float2 v = __fadd2_rn(s, neg2(sh));
-  const float2 e = __fadd2_rn(__fadd2_rn(sh, neg2(__fadd2_rn(s, neg2(v)))),
-                              __fadd2_rn(ah, neg2(v)));
-  sh = s;
-  sl = __fadd2_rn(sl, __fadd2_rn(al, e));
+// a - b is formed as fma(b, -1, a): the product is exact, so the result is the
+// correctly rounded difference, in one instruction without a negated operand.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
-__device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float wh, float wl, float2 uh,
-                                        float2 ul) {
-  const float2 w = make_float2(wh, wh), v = make_float2(wl, wl);
+// (sh, sl) += (ah, al - q): two-sum of the high parts; the low part arrives
+// as al and a term q to subtract (q = 0.f2 when there is none).
+__device__ __forceinline__ void df_add2(float2& sh, float2& sl, float2 ah, float2 al, float2 q) {
+  const float2 s = __fadd2_rn(sh, ah);
+  const float2 v = sub2(s, sh);
+  const float2 e = __fadd2_rn(sub2(sh, sub2(s, v)), sub2(ah, v));
+  sh = s;
+  sl = __fadd2_rn(sl, __fadd2_rn(al, sub2(e, q)));
+}
+
+// (sh, sl) -= (ah, al): two-sum of sh and -ah written with subtractions
+// (each rounding is symmetric under negation, so the error term is exact).
+__device__ __forceinline__ void df_sub2(float2& sh, float2& sl, float2 ah, float2 al) {
+  const float2 s = sub2(sh, ah);
+  const float2 v = sub2(s, sh);
+  const float2 e = sub2(sub2(sh, sub2(s, v)), __fadd2_rn(ah, v));
+  sh = s;
+  sl = __fadd2_rn(sl, sub2(e, al));
+}
+
+// (sh, sl) += (wh + wl)(uh + ul).  With nw = -wh, nv = -wl:
+// ph = wh uh, q = ph - wh uh (exact, = minus the product's error) - wh ul - wl uh.
+__device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float wh, float nw, float nv,
+                                        float2 uh, float2 ul) {
+  const float2 w = make_float2(wh, wh), wn = make_float2(nw, nw), vn = make_float2(nv, nv);
   const float2 ph = __fmul2_rn(w, uh);
-  float2 pl = __ffma2_rn(w, uh, neg2(ph));
-  pl = __ffma2_rn(w, ul, pl);
-  pl = __ffma2_rn(v, uh, pl);
-  df_add2(sh, sl, ph, pl);
+  float2 q = __ffma2_rn(wn, uh, ph);
+  q = __ffma2_rn(wn, ul, q);
+  q = __ffma2_rn(vn, uh, q);
+  df_add2(sh, sl, ph, make_float2(0.f, 0.f), q);
 }
 
 // Shared-memory kernel: block (x, y) takes the tile of T = 256 * SM_NR nodes
@@ -339,14 +356,14 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
     const int i = p - q0;
     const float4 c0 = su[i], cw = su[i - 1], ce = su[i + 1], cs = su[i - mx], cn = su[i + mx];
     float2 ah = make_float2(bha, bhb), al = make_float2(bla, blb);
-    if (lift) df_add2(ah, al, make_float2(lh, lh), make_float2(ll, ll));
-    df_add2(ah, al, make_float2(-c0.x, -c0.y), make_float2(-c0.z, -c0.w));
-    df_fma2(ah, al, wh.x, wl.x, make_float2(cw.x, cw.y), make_float2(cw.z, cw.w));
-    df_fma2(ah, al, wh.y, wl.y, make_float2(ce.x, ce.y), make_float2(ce.z, ce.w));
-    df_fma2(ah, al, wh.z, wl.z, make_float2(cs.x, cs.y), make_float2(cs.z, cs.w));
-    df_fma2(ah, al, wh.w, wl.w, make_float2(cn.x, cn.y), make_float2(cn.z, cn.w));
+    if (lift) df_add2(ah, al, make_float2(lh, lh), make_float2(ll, ll), make_float2(0.f, 0.f));
+    df_sub2(ah, al, make_float2(c0.x, c0.y), make_float2(c0.z, c0.w));
+    df_fma2(ah, al, wh.x, -wh.x, -wl.x, make_float2(cw.x, cw.y), make_float2(cw.z, cw.w));
+    df_fma2(ah, al, wh.y, -wh.y, -wl.y, make_float2(ce.x, ce.y), make_float2(ce.z, ce.w));
+    df_fma2(ah, al, wh.z, -wh.z, -wl.z, make_float2(cs.x, cs.y), make_float2(cs.z, cs.w));
+    df_fma2(ah, al, wh.w, -wh.w, -wl.w, make_float2(cn.x, cn.y), make_float2(cn.z, cn.w));
     const float2 s = __fadd2_rn(ah, al);
-    const float2 e = __fadd2_rn(al, neg2(__fadd2_rn(s, neg2(ah))));
+    const float2 e = sub2(al, sub2(s, ah));
     float sa = s.x, ea = e.x, sb = s.y, eb = e.y;
     if (!(fmaxf(fmaxf(fabsf(c0.x), fabsf(bha)), fabsf(lh)) >= 0x1p-60f) ||
         !(fabsf(sa) <= 3.4028234e38f))
