@@ -327,7 +327,6 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
   const bool has_b = cb < B;
   const double* ua = u + (size_t)ca * n;
   const double* ub = u + (size_t)(has_b ? cb : ca) * n;
-#pragma unroll 4
   for (int i = threadIdx.x; i < L; i += 256) {
     const int q = q0 + i;
     float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
@@ -344,7 +343,7 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
   float mxa = 0.f, mxb = 0.f;
   const double* ba = b + (size_t)ca * n;
   const double* bb = b + (size_t)(has_b ? cb : ca) * n;
-#pragma unroll 4
+#pragma unroll 2
   for (int k = 0; k < SM_NR; ++k) {
     const int p = P0 + (int)threadIdx.x + 256 * k;
     if (p >= n) break;
