@@ -72,6 +72,12 @@ typedef struct {
   double h;        /* grid spacing (Eq. 2), > 0 */
 } pide_grid;
 
+/* A 3-D node grid: nx x ny x nz nodes including boundary nodes, spacing h. */
+typedef struct {
+  int32_t nx, ny, nz;   /* each >= 3 */
+  double h;
+} pide_grid3;
+
 typedef struct {
   int32_t sweeps;        /* refinement sweeps executed */
   int32_t converged;     /* 1 if tol was met (always 1 when tol <= 0) */
@@ -86,6 +92,7 @@ typedef struct {
   int32_t num_sms;       /* SMs of the device the handle lives on */
   size_t store_bytes;    /* bytes of the stored inverse (+ scales) read per apply */
   double setup_ms;
+  int32_t dims;          /* 2 (pide_setup) or 3 (pide_setup_3d) */
 } pide_handle_info;
 
 /* Per-kernel-class event timing, recorded on the launching stream. */
@@ -114,6 +121,24 @@ typedef struct {
  */
 pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
                        void* stream, pide_handle* out);
+
+/*
+ * pide_setup_3d -- the same for an nx x ny x nz node grid (the paper states its
+ * problem for N grid points; the worked case is 2-D): the 7-point flux form
+ * with harmonic face permittivity, each interior row divided by its total face
+ * permittivity (weight 1/6 at eps = 1), identity rows at boundary nodes.
+ *   eps_host  [nz][ny][nx] node permittivity (x fastest), or NULL for eps = 1.
+ * Interior unknowns p = ((k-1)(ny-2) + (i-1))(nx-2) + (j-1) for node (k, i, j)
+ * (z, y, x).  The handle serves pide_apply, pide_apply_host, pide_solve_stream,
+ * pide_residual, pide_rhs_from_charge (b = -h^2 rho / d with the six-face d),
+ * boundary values g [nz][ny][nx] in pide_apply, the tuning and profiling
+ * hooks, and pide_apply_backward without dLoss/deps.  pide_save, the batched
+ * plans and pide_apply_noalloc return PIDE_EUNSUPPORTED for it.  The FP64
+ * inverse is formed by block elimination over z-planes: setup cost grows as
+ * ((nx-2)(ny-2))^3 (nz-2) on GB300's FP64 pipe (seconds at 32^3 unknowns).
+ */
+pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host, pide_precision p,
+                          void* stream, pide_handle* out);
 
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void pide_destroy(pide_handle h);

@@ -24,6 +24,11 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double)]
 
 
+class Grid3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("h", ctypes.c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double)]
@@ -32,7 +37,7 @@ class Info(ctypes.Structure):
 class HandleInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("ld", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("num_sms", ctypes.c_int32), ("store_bytes", ctypes.c_size_t),
-                ("setup_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("dims", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -52,6 +57,7 @@ _I = ctypes.c_int32
 _D = ctypes.c_double
 _SIGS = {
     "pide_setup": (_I, [ctypes.POINTER(Grid), _P, _I, _P, ctypes.POINTER(_P)]),
+    "pide_setup_3d": (_I, [ctypes.POINTER(Grid3), _P, _I, _P, ctypes.POINTER(_P)]),
     "pide_destroy": (None, [_P]),
     "pide_apply": (_I, [_P, _P, _P, _I, _I, _D, _P, _P, ctypes.POINTER(Info)]),
     "pide_apply_host": (_I, [_P, _P, _P, _I, _I, _D, _P, ctypes.POINTER(Info)]),
@@ -265,17 +271,22 @@ class Solver:
                                              _stream(stream)), "pide_rhs_from_charge")
         return b
 
-    def backward(self, gout, u, b, sweeps: int = 4, stream=None):
-        """(dLoss/db, dLoss/deps) for u = L(eps)^-1 b given gout = dLoss/du."""
+    def backward(self, gout, u, b, sweeps: int = 4, stream=None, want_deps: bool = True):
+        """(dLoss/db, dLoss/deps) for u = L(eps)^-1 b given gout = dLoss/du
+        (deps is None when want_deps is False)."""
         import torch
         gout = _as_dev(gout, self.device).reshape(-1, self.n)
         u = _as_dev(u, self.device).reshape(-1, self.n)
         b = _as_dev(b, self.device).reshape(-1, self.n)
         db = torch.empty_like(gout)
-        deps = torch.zeros((self.ny, self.nx), dtype=torch.float64, device=self.device)
+        deps = None
+        if want_deps:
+            shape = (self.ny, self.nx) if not hasattr(self, "nz") else (self.nz, self.ny, self.nx)
+            deps = torch.zeros(shape, dtype=torch.float64, device=self.device)
         _check(self.lib.pide_apply_backward(self.handle, _ptr(gout), _ptr(u), _ptr(b), _ptr(db),
-                                            _ptr(deps), gout.shape[0], int(sweeps),
-                                            _stream(stream)), "pide_apply_backward")
+                                            _ptr(deps) if deps is not None else None,
+                                            gout.shape[0], int(sweeps), _stream(stream)),
+               "pide_apply_backward")
         return db, deps
 
     TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3,
@@ -343,6 +354,34 @@ class Solver:
             _check(self.lib.pide_profile_end(self.handle, ctypes.byref(p)), "pide_profile_end")
             for i, name in enumerate(["apply", "residual", "prep", "other"]):
                 out[name] = (int(p.launches[i]), float(p.ms[i]))
+
+
+class Solver3D(Solver):
+    """The same on an nx x ny x nz node grid (pide_setup_3d): eps is
+    [nz][ny][nx]; right-hand sides and solutions are [B][(nx-2)(ny-2)(nz-2)],
+    x fastest; boundary values g are [nz][ny][nx]."""
+
+    def __init__(self, nx: int, ny: int, nz: int, h: float, eps=None, precision: str = "bf16",
+                 stream=None):
+        import torch
+        self.lib = load_library()
+        self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
+        self.n = (self.nx - 2) * (self.ny - 2) * (self.nz - 2)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        g = Grid3(self.nx, self.ny, self.nz, self.h)
+        eps_p = None
+        self._eps_keep = None
+        if eps is not None:
+            e = np.ascontiguousarray(
+                np.asarray(eps, dtype=np.float64).reshape(self.nz, self.ny, self.nx))
+            self._eps_keep = e
+            eps_p = e.ctypes.data_as(ctypes.c_void_p)
+        h_out = ctypes.c_void_p()
+        _check(self.lib.pide_setup_3d(ctypes.byref(g), eps_p, PRECISIONS[precision],
+                                      _stream(stream), ctypes.byref(h_out)), "pide_setup_3d")
+        self.handle = h_out
+        self.eps = None if eps is None else self._eps_keep
 
 
 def apply_batched(solvers, bs, us, sweeps: int = 2, stream=None):

@@ -292,16 +292,20 @@ static bool valid_grid(const pide_grid* g) {
          (int64_t)(g->nx - 2) * (g->ny - 2) < (int64_t)1 << 30;
 }
 
-static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double* eps_host,
-                                  cudaStream_t st) {
-  c->nx = g->nx;
-  c->ny = g->ny;
-  c->h = g->h;
-  c->mx = g->nx - 2;
-  c->my = g->ny - 2;
-  c->n = c->mx * c->my;
+static pide_status setup_operator(pide_ctx* c, int nx, int ny, int nz, double h, int dims,
+                                  const double* eps_host, cudaStream_t st) {
+  c->dims = dims;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = dims == 3 ? nz : 1;
+  c->h = h;
+  c->mx = nx - 2;
+  c->my = ny - 2;
+  c->mz = dims == 3 ? nz - 2 : 1;
+  c->n = c->mx * c->my * c->mz;
   c->ld = ((c->n + 63) / 64) * 64;
-  const size_t N = (size_t)c->nx * c->ny;
+  const size_t N = (size_t)nx * ny * c->nz;
+  const int faces = dims == 3 ? 6 : 4;
   c->eps_host.assign(N, 1.0);
   if (eps_host) {
     for (size_t k = 0; k < N; ++k) {
@@ -322,10 +326,10 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   }
   c->num_sms = prop.multiProcessorCount;
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->eps, N * sizeof(double)));
-  PIDE_CUDA_TRY(cudaMalloc((void**)&c->cf, 4 * (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->cf, faces * (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->d, (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->dinv, (size_t)c->n * sizeof(double)));
-  PIDE_CUDA_TRY(cudaMalloc((void**)&c->w, 4 * (size_t)c->n * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->w, faces * (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->lift, (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->flags, FLAG_COUNT * sizeof(uint32_t)));
 
@@ -341,20 +345,17 @@ static pide_status setup_operator(pide_ctx* c, const pide_grid* g, const double*
   PIDE_CUDA_TRY(cudaMemcpyAsync(c->eps, c->eps_host.data(), N * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
   PIDE_TRY(launch_assemble(c, st));
-  PIDE_CUDA_TRY(cudaMalloc((void**)&c->wsp, 2 * (size_t)c->n * sizeof(float4)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->wsp, (dims == 3 ? 3 : 2) * (size_t)c->n * sizeof(float4)));
   PIDE_TRY(launch_wsplit(c, st));
   return PIDE_OK;
 }
 
-extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
-                                  void* stream, pide_handle* out) {
-  if (out) *out = nullptr;
-  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 4) {
-    set_error("pide_setup: bad argument");
-    return PIDE_EINVAL;
-  }
+// Steps 1-2 for a 2-D (dims 2) or 3-D (dims 3) grid: assemble, invert in FP64,
+// quantise; the handle is returned only when every step succeeded.
+static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, const double* eps_host,
+                                pide_precision p, void* stream, pide_handle* out) {
   if (eps_host) {
-    const size_t N = (size_t)g->nx * g->ny;
+    const size_t N = (size_t)nx * ny * (dims == 3 ? nz : 1);
     for (size_t k = 0; k < N; ++k)
       if (!std::isfinite(eps_host[k]) || !(eps_host[k] > 0.0)) {
         set_error("eps must be finite and > 0 at every node");
@@ -372,7 +373,7 @@ extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pi
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
   c->prec = p;
-  pide_status s = setup_operator(c, g, eps_host, st);
+  pide_status s = setup_operator(c, nx, ny, nz, h, dims, eps_host, st);
   double* G = nullptr;
   if (s == PIDE_OK) {
     const size_t bytes = (size_t)c->n * c->ld * sizeof(double);
@@ -413,6 +414,28 @@ extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pi
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = c;
   return PIDE_OK;
+}
+
+extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
+                                  void* stream, pide_handle* out) {
+  if (out) *out = nullptr;
+  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 4) {
+    set_error("pide_setup: bad argument");
+    return PIDE_EINVAL;
+  }
+  return setup_handle(g->nx, g->ny, 1, g->h, 2, eps_host, p, stream, out);
+}
+
+extern "C" pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host,
+                                     pide_precision p, void* stream, pide_handle* out) {
+  if (out) *out = nullptr;
+  const bool ok = g && g->nx >= 3 && g->ny >= 3 && g->nz >= 3 && std::isfinite(g->h) && g->h > 0 &&
+                  (int64_t)(g->nx - 2) * (g->ny - 2) * (g->nz - 2) < (int64_t)1 << 30;
+  if (!out || !ok || (int)p < 0 || (int)p > 4) {
+    set_error("pide_setup_3d: bad argument");
+    return PIDE_EINVAL;
+  }
+  return setup_handle(g->nx, g->ny, g->nz, g->h, 3, eps_host, p, stream, out);
 }
 
 extern "C" void pide_destroy(pide_handle h) {
@@ -618,6 +641,10 @@ extern "C" pide_status pide_apply_backward(pide_handle h, const double* gout_dev
     set_error("pide_apply_backward: b_dev is required");
     return PIDE_EINVAL;
   }
+  if (h->dims == 3 && deps_dev) {
+    set_error("pide_apply_backward: dLoss/deps is built for 2-D grids only (pass deps_dev = NULL)");
+    return PIDE_EUNSUPPORTED;
+  }
   if (B == 0) return PIDE_OK;
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -683,6 +710,10 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
   if (!h || !path) {
     set_error("pide_save: bad argument");
     return PIDE_EINVAL;
+  }
+  if (h->dims == 3) {
+    set_error("pide_save: the file format holds 2-D grids only");
+    return PIDE_EUNSUPPORTED;
   }
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
   PIDE_CUDA_TRY(cudaDeviceSynchronize());
@@ -756,7 +787,7 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
   c->prec = (pide_precision)hd.prec;
-  pide_status s = setup_operator(c, &g, eps.data(), st);
+  pide_status s = setup_operator(c, g.nx, g.ny, 1, g.h, 2, eps.data(), st);
   if (s == PIDE_OK && (c->n != hd.n || c->ld != hd.ld)) {
     set_error("pide_load: header sizes do not match the grid");
     s = PIDE_EINVAL;
@@ -814,6 +845,7 @@ extern "C" pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out
   out->num_sms = h->num_sms;
   out->store_bytes = h->store_bytes;
   out->setup_ms = h->setup_ms;
+  out->dims = h->dims;
   return PIDE_OK;
 }
 

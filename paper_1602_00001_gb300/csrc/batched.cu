@@ -381,6 +381,11 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
     set_error("pide_batch_create: bad argument");
     return PIDE_EINVAL;
   }
+  for (int k = 0; k < nprob; ++k)
+    if (hs[k] && hs[k]->dims == 3) {
+      set_error("pide_batch_create: batched problems are 2-D grids");
+      return PIDE_EUNSUPPORTED;
+    }
   pide_batch* p = new pide_batch();
   std::vector<BatchProb> probs(nprob);
   struct Item { int prob, mt, ct; double cost; };

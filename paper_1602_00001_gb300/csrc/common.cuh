@@ -50,18 +50,20 @@ struct pide_ctx_impl;
 }  // namespace pide
 
 struct pide_ctx {
-  // grid and operator
-  int nx = 0, ny = 0, mx = 0, my = 0, n = 0;
+  // grid and operator (dims 2: nx x ny nodes; dims 3: nx x ny x nz nodes, x fastest)
+  int dims = 2;
+  int nx = 0, ny = 0, nz = 1, mx = 0, my = 0, mz = 1, n = 0;
   double h = 0.0;
   pide_precision prec = PIDE_FP64;
   int device = 0, num_sms = 0;
   int ld = 0;                       // row stride of the stored inverse (elements)
-  double* eps = nullptr;            // [ny][nx] node permittivity
-  double* cf = nullptr;             // [4][n] face eps of each interior node: W, E, S, N
+  double* eps = nullptr;            // [(nz)][ny][nx] node permittivity
+  double* cf = nullptr;             // [4 or 6][n] face eps of each interior node: W, E, S, N (, D, U)
   double* d = nullptr;              // [n] diagonal of S (sum of face eps)
   double* dinv = nullptr;           // [n] 1 / d
-  double* w = nullptr;              // [4][n] Eq. (3) weights w = cf / d
-  float4* wsp = nullptr;            // [2][n] w as float pairs (hi, lo), zero toward boundary nodes
+  double* w = nullptr;              // [4 or 6][n] Eq. (3) weights w = cf / d
+  float4* wsp = nullptr;            // [2 or 3][n] w as float pairs, zero toward boundary nodes:
+                                    // (W,E,S,N) hi, (W,E,S,N) lo (, (D hi, U hi, D lo, U lo))
   std::vector<double> eps_host;     // kept for save/load
   // stored inverse L^-1 = S^-1 D (the interior block of the Fig. 3 inverse)
   void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / e4m3 (hi)
@@ -123,6 +125,11 @@ struct pide_ctx {
 };
 
 namespace pide {
+
+// Nodes in one z-plane of the interior (3-D), or all of them (2-D): the
+// distance between up/down neighbours, and the bound that makes the 2-D
+// stencil's up/down terms vanish.
+inline int plane_of(const pide_ctx* c) { return c->dims == 3 ? c->mx * c->my : c->n; }
 
 // ---------------------------------------------------------------- launchers
 // (each returns a pide_status; kernels are enqueued on `st`)

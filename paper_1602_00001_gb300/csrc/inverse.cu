@@ -1,12 +1,16 @@
 // Step 2 ("using any standard matrix inversion method"): the dense inverse of
 // the symmetric conservative operator S = D L, formed in FP64 on the GPU.
 //
-// S is block tridiagonal over grid rows: m = ny-2 diagonal blocks A_a (k x k,
-// k = nx-2, tridiagonal: d on the diagonal, -eps of the x faces beside it) and
-// diagonal couplings S_{a,a+1} = -diag(eps of the y faces between rows a, a+1).
+// S is block tridiagonal over the slowest grid index: on a 2-D grid the m =
+// ny-2 blocks are grid rows (k = nx-2 nodes, A_a tridiagonal: d on the
+// diagonal, -eps of the x faces beside it), on a 3-D grid the m = nz-2 blocks
+// are z-planes (k = (nx-2)(ny-2) nodes, A_a the in-plane 5-point operator:
+// -eps of the x faces at distance 1 within a row, of the y faces at distance
+// nx-2).  The couplings S_{a,a+1} = -diag(eps of the faces between blocks a and
+// a+1) are diagonal in both cases (y faces in 2-D, z faces in 3-D).
 // Block elimination from both ends gives the whole inverse G = S^-1:
 //   backward Schur complements  Sg_{m-1} = A_{m-1},
-//                               Sg_a = A_a - C_a Sg_{a+1}^-1 C_a      (C_a = diag(north faces of row a))
+//                               Sg_a = A_a - C_a Sg_{a+1}^-1 C_a      (C_a = faces to block a+1)
 //   forward Schur complements   Df_0 = A_0,
 //                               Df_a = A_a - C_{a-1} Df_{a-1}^-1 C_{a-1}
 //   diagonal blocks             G_aa = (A_a - C_{a-1} Df_{a-1}^-1 C_{a-1} - C_a Sg_{a+1}^-1 C_a)^-1
@@ -49,25 +53,43 @@ __device__ void gj_invert(double* A, int k, size_t lda, double* s_row, double* s
   }
 }
 
-__device__ __forceinline__ double block_A(const double* cf, const double* d, int n, int k, int a,
-                                          int r, int c) {
-  const int p = a * k + r;
-  if (r == c) return d[p];
-  if (c == r + 1) return -cf[n + p];        // east face of (a, r)
-  if (c == r - 1) return -cf[p];            // west face of (a, r)
+// The block structure: k nodes per block, m blocks, rows of mxb nodes inside
+// a block when the block is a 3-D plane (mxb = 0: the block is one 2-D row),
+// face arrays of the in-block neighbours and of the couplings to the next and
+// the previous block.
+struct BlockOp {
+  const double* cf;   // face eps, structure of arrays: W, E, S, N (, D, U)
+  const double* d;
+  int n, k, m, mxb;
+  int f_next, f_prev;  // face array index of the coupling to block a+1 / a-1
+};
+
+__device__ __forceinline__ double block_A(const BlockOp& op, int a, int r, int c) {
+  const int p = a * op.k + r;
+  const size_t n = (size_t)op.n;
+  if (r == c) return op.d[p];
+  if (op.mxb == 0) {                        // 2-D: tridiagonal grid row
+    if (c == r + 1) return -op.cf[n + p];   // east face of (a, r)
+    if (c == r - 1) return -op.cf[p];       // west face of (a, r)
+    return 0.0;
+  }
+  const int x = r % op.mxb;                 // 3-D: 5-point plane operator
+  if (c == r + 1 && x < op.mxb - 1) return -op.cf[n + p];
+  if (c == r - 1 && x > 0) return -op.cf[p];
+  if (c == r + op.mxb) return -op.cf[3 * n + p];
+  if (c == r - op.mxb) return -op.cf[2 * n + p];
   return 0.0;
 }
 
 // blockIdx.x == 0: backward chain into Gb[a] = Sg_a^-1; == 1: forward chain into Gf[a] = Df_a^-1.
-__global__ void __launch_bounds__(1024) chain_kernel(const double* __restrict__ cf,
-                                                     const double* __restrict__ d, int k, int m,
-                                                     double* __restrict__ Gb,
+__global__ void __launch_bounds__(1024) chain_kernel(BlockOp op, double* __restrict__ Gb,
                                                      double* __restrict__ Gf) {
   extern __shared__ double sh[];
+  const int k = op.k, m = op.m;
   double* s_row = sh;
   double* s_col = sh + k;
   double* s_rp = sh + 2 * k;
-  const int n = k * m;
+  const size_t n = (size_t)op.n;
   const bool backward = (blockIdx.x == 0);
   const size_t kk = (size_t)k * k;
   for (int step = 0; step < m; ++step) {
@@ -75,11 +97,11 @@ __global__ void __launch_bounds__(1024) chain_kernel(const double* __restrict__ 
     double* T = (backward ? Gb : Gf) + (size_t)a * kk;
     const bool has_prev = backward ? (a < m - 1) : (a > 0);
     const double* P = has_prev ? ((backward ? Gb : Gf) + (size_t)(backward ? a + 1 : a - 1) * kk) : nullptr;
-    // coupling faces: backward uses the north faces of row a, forward the south faces of row a
-    const double* C = backward ? (cf + 3 * (size_t)n + (size_t)a * k) : (cf + 2 * (size_t)n + (size_t)a * k);
+    // coupling faces: backward to block a+1, forward to block a-1
+    const double* C = op.cf + (size_t)(backward ? op.f_next : op.f_prev) * n + (size_t)a * k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
       const int r = e / k, c = e - r * k;
-      double v = block_A(cf, d, n, k, a, r, c);
+      double v = block_A(op, a, r, c);
       if (has_prev) v -= C[r] * P[e] * C[c];
       T[e] = v;
     }
@@ -90,23 +112,22 @@ __global__ void __launch_bounds__(1024) chain_kernel(const double* __restrict__ 
 
 // Diagonal blocks of the inverse, one CTA per block row a, written in place
 // into G at block (a, a).
-__global__ void __launch_bounds__(1024) diag_kernel(const double* __restrict__ cf,
-                                                    const double* __restrict__ d, int k, int m,
-                                                    const double* __restrict__ Gb,
+__global__ void __launch_bounds__(1024) diag_kernel(BlockOp op, const double* __restrict__ Gb,
                                                     const double* __restrict__ Gf,
                                                     double* __restrict__ G, size_t ld) {
   extern __shared__ double sh[];
   const int a = blockIdx.x;
-  const int n = k * m;
+  const int k = op.k, m = op.m;
+  const size_t n = (size_t)op.n;
   const size_t kk = (size_t)k * k;
   double* T = G + (size_t)a * k * ld + (size_t)a * k;
-  const double* Cs = cf + 2 * (size_t)n + (size_t)a * k;
-  const double* Cn = cf + 3 * (size_t)n + (size_t)a * k;
+  const double* Cs = op.cf + (size_t)op.f_prev * n + (size_t)a * k;
+  const double* Cn = op.cf + (size_t)op.f_next * n + (size_t)a * k;
   const double* Pf = (a > 0) ? Gf + (size_t)(a - 1) * kk : nullptr;
   const double* Pb = (a < m - 1) ? Gb + (size_t)(a + 1) * kk : nullptr;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int r = e / k, c = e - r * k;
-    double v = block_A(cf, d, n, k, a, r, c);
+    double v = block_A(op, a, r, c);
     if (Pf) v -= Cs[r] * Pf[e] * Cs[c];
     if (Pb) v -= Cn[r] * Pb[e] * Cn[c];
     T[(size_t)r * ld + c] = v;
@@ -115,16 +136,16 @@ __global__ void __launch_bounds__(1024) diag_kernel(const double* __restrict__ c
   gj_invert(T, k, ld, sh, sh + k, sh + 2 * k);
 }
 
-// M_a = Sg_a^-1 diag(south faces of row a) for a >= 1, in place over Gb[a].
-__global__ void mscale_kernel(const double* __restrict__ cf, int k, int m, double* __restrict__ Gb) {
-  const int n = k * m;
+// M_a = Sg_a^-1 diag(faces of block a to block a-1) for a >= 1, in place over Gb[a].
+__global__ void mscale_kernel(BlockOp op, double* __restrict__ Gb) {
+  const int k = op.k, m = op.m;
   const size_t kk = (size_t)k * k;
   const size_t total = (size_t)(m - 1) * kk;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int a = 1 + (int)(e / kk);
     const int c = (int)((e % kk) % k);
-    Gb[kk + e] *= cf[2 * (size_t)n + (size_t)a * k + c];
+    Gb[kk + e] *= op.cf[(size_t)op.f_prev * op.n + (size_t)a * k + c];
   }
 }
 
@@ -215,19 +236,25 @@ __global__ void mirror_kernel(double* __restrict__ G, size_t ld, int n, int k) {
 }  // namespace
 
 pide_status build_inverse_fp64(pide_ctx* c, double* G, cudaStream_t st) {
-  const int k = c->mx, m = c->my;
+  const bool three = c->dims == 3;
+  const int k = three ? c->mx * c->my : c->mx, m = three ? c->mz : c->my;
+  const BlockOp op{c->cf, c->d, c->n, k, m, three ? c->mx : 0, three ? 5 : 3, three ? 4 : 2};
   const size_t kk = (size_t)k * k;
   double* work = nullptr;
   PIDE_CUDA_TRY(cudaMallocAsync((void**)&work, 2 * (size_t)m * kk * sizeof(double), st));
   double* Gb = work;
   double* Gf = work + (size_t)m * kk;
   const size_t shm = 3 * (size_t)k * sizeof(double);
-  chain_kernel<<<2, 1024, shm, st>>>(c->cf, c->d, k, m, Gb, Gf);
+  if (shm > 48 * 1024) {
+    PIDE_CUDA_TRY(cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    PIDE_CUDA_TRY(cudaFuncSetAttribute(diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  }
+  chain_kernel<<<2, 1024, shm, st>>>(op, Gb, Gf);
   PIDE_CUDA_TRY(cudaGetLastError());
-  diag_kernel<<<m, 1024, shm, st>>>(c->cf, c->d, k, m, Gb, Gf, G, (size_t)c->ld);
+  diag_kernel<<<m, 1024, shm, st>>>(op, Gb, Gf, G, (size_t)c->ld);
   PIDE_CUDA_TRY(cudaGetLastError());
   if (m > 1) {
-    mscale_kernel<<<c->num_sms * 4, 256, 0, st>>>(c->cf, k, m, Gb);
+    mscale_kernel<<<c->num_sms * 4, 256, 0, st>>>(op, Gb);
     PIDE_CUDA_TRY(cudaGetLastError());
     const int tiles = (k + 63) / 64;
     for (int s = 1; s < m; ++s) {

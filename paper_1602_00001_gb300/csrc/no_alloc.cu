@@ -152,6 +152,10 @@ extern "C" pide_status pide_apply_noalloc(pide_handle h, const double* b_dev, do
               std::to_string(h->n) + "); use pide_apply for larger problems");
     return PIDE_EINVAL;
   }
+  if (h->dims == 3) {
+    set_error("pide_apply_noalloc: 2-D grids only");
+    return PIDE_EUNSUPPORTED;
+  }
   if (B == 0) return PIDE_OK;
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
   float* R = nullptr;

@@ -44,6 +44,54 @@ __global__ void assemble_kernel(const double* __restrict__ eps, int nx, int ny,
   }
 }
 
+// The same on an nx x ny x nz node grid (the 7-point flux form): six faces per
+// interior node p = (z*my + y)*mx + x, in the order W, E, S, N, D, U.
+__global__ void assemble3d_kernel(const double* __restrict__ eps, int nx, int ny, int nz,
+                                  double* __restrict__ cf, double* __restrict__ d,
+                                  double* __restrict__ w6, double* __restrict__ dinv) {
+  const int mx = nx - 2, my = ny - 2, mz = nz - 2;
+  const int n = mx * my * mz;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int x = p % mx, y = (p / mx) % my, z = p / (mx * my);
+    const size_t sx = 1, sy = nx, sz = (size_t)nx * ny;
+    const size_t q = (size_t)(z + 1) * sz + (size_t)(y + 1) * sy + (x + 1);
+    const double e0 = eps[q];
+    const double f[6] = {harmonic(e0, eps[q - sx]), harmonic(e0, eps[q + sx]),
+                         harmonic(e0, eps[q - sy]), harmonic(e0, eps[q + sy]),
+                         harmonic(e0, eps[q - sz]), harmonic(e0, eps[q + sz])};
+    double dp = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      cf[(size_t)k * n + p] = f[k];
+      dp += f[k];
+    }
+    d[p] = dp;
+    dinv[p] = 1.0 / dp;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w6[(size_t)k * n + p] = f[k] / dp;
+  }
+}
+
+// 3-D lift: lift_p = sum over boundary neighbours q of w_pq g_q, g = [nz][ny][nx].
+__global__ void lift3d_kernel(const double* __restrict__ g, const double* __restrict__ w6, int nx,
+                              int ny, int nz, double* __restrict__ lift) {
+  const int mx = nx - 2, my = ny - 2, mz = nz - 2;
+  const int n = mx * my * mz;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int x = p % mx, y = (p / mx) % my, z = p / (mx * my);
+    const size_t sy = nx, sz = (size_t)nx * ny;
+    const size_t q = (size_t)(z + 1) * sz + (size_t)(y + 1) * sy + (x + 1);
+    double s = 0.0;
+    if (x == 0) s += w6[p] * g[q - 1];
+    if (x == mx - 1) s += w6[(size_t)n + p] * g[q + 1];
+    if (y == 0) s += w6[2 * (size_t)n + p] * g[q - sy];
+    if (y == my - 1) s += w6[3 * (size_t)n + p] * g[q + sy];
+    if (z == 0) s += w6[4 * (size_t)n + p] * g[q - sz];
+    if (z == mz - 1) s += w6[5 * (size_t)n + p] * g[q + sz];
+    lift[p] = s;
+  }
+}
+
 // b = -h^2 rho / d  (flux form of Eq. 1 divided by the node's total face eps)
 __global__ void rhs_from_charge_kernel(const double* __restrict__ rho, double* __restrict__ b,
                                        const double* __restrict__ d, int n, long long total,
@@ -136,7 +184,8 @@ __global__ void prep_kernel(const double* __restrict__ b, int n, int ldr, int mo
 // optionally in full to r_out, and its column max |r| into colmax_r.
 template <int RF>
 __global__ void residual_kernel(const double* __restrict__ b, const double* __restrict__ u,
-                                int n, int mx, int ldr, int mode, const double* __restrict__ w4,
+                                int n, int mx, int plane, int ldr, int mode,
+                                const double* __restrict__ w4,
                                 const double* __restrict__ dinv, const double* __restrict__ lift,
                                 void* __restrict__ R, const float* __restrict__ col_scale,
                                 double* __restrict__ r_out, double* __restrict__ colmax_r,
@@ -149,15 +198,17 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
   const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
   double mxr = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int c = p % mx;
+    const int c = p % mx, pp = p % plane;   // x, and the index inside a z-plane
     double r;
     if (mode == 1) r = fma(bc[p], dinv[p], -uc[p]);
     else if (lift) r = bc[p] + (lift[p] - uc[p]);
     else r = bc[p] - uc[p];
     if (c > 0) r = fma(w4[p], uc[p - 1], r);
     if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
-    if (p >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
-    if (p + mx < n) r = fma(w4[3 * n + p], uc[p + mx], r);
+    if (pp >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
+    if (pp + mx < plane) r = fma(w4[3 * n + p], uc[p + mx], r);
+    if (p >= plane) r = fma(w4[4 * (size_t)n + p], uc[p - plane], r);          // 3-D only
+    if (p + plane < n) r = fma(w4[5 * (size_t)n + p], uc[p + plane], r);
     if (R) store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
     if (r_out) r_out[(size_t)col * n + p] = r;
     if (track) mxr = fmax(mxr, fabs(r));
@@ -174,7 +225,7 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
 // and MMA issuers depend on.
 template <int RF>
 __global__ void residual_flat_kernel(const double* __restrict__ b, const double* __restrict__ u,
-                                     int n, int mx, int B, int ldr, int mode,
+                                     int n, int mx, int plane, int B, int ldr, int mode,
                                      const double* __restrict__ w4,
                                      const double* __restrict__ dinv,
                                      const double* __restrict__ lift, void* __restrict__ R,
@@ -186,7 +237,7 @@ __global__ void residual_flat_kernel(const double* __restrict__ b, const double*
        k += (long long)gridDim.x * blockDim.x) {
     const int col = (int)(k / n);
     const int p = (int)(k - (long long)col * n);
-    const int c = p % mx;
+    const int c = p % mx, pp = p % plane;
     const double* uc = u + (size_t)col * n;
     // streaming loads (evict-first): keep the concurrent GEMM's operands in L2
     const double bp = __ldcs(b + k);
@@ -197,8 +248,10 @@ __global__ void residual_flat_kernel(const double* __restrict__ b, const double*
     else r = bp - up;
     if (c > 0) r = fma(w4[p], __ldcs(uc + p - 1), r);
     if (c < mx - 1) r = fma(w4[n + p], __ldcs(uc + p + 1), r);
-    if (p >= mx) r = fma(w4[2 * n + p], __ldcs(uc + p - mx), r);
-    if (p + mx < n) r = fma(w4[3 * n + p], __ldcs(uc + p + mx), r);
+    if (pp >= mx) r = fma(w4[2 * n + p], __ldcs(uc + p - mx), r);
+    if (pp + mx < plane) r = fma(w4[3 * n + p], __ldcs(uc + p + mx), r);
+    if (p >= plane) r = fma(w4[4 * (size_t)n + p], __ldcs(uc + p - plane), r);
+    if (p + plane < n) r = fma(w4[5 * (size_t)n + p], __ldcs(uc + p + plane), r);
     const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
     store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
   }
@@ -298,8 +351,12 @@ inline int grid_for(long long work, int block, int num_sms) {
 }  // namespace
 
 pide_status launch_assemble(pide_ctx* c, cudaStream_t st) {
-  assemble_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(c->eps, c->nx, c->ny, c->cf,
-                                                                    c->d, c->w, c->dinv);
+  if (c->dims == 3)
+    assemble3d_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(c->eps, c->nx, c->ny, c->nz,
+                                                                        c->cf, c->d, c->w, c->dinv);
+  else
+    assemble_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(c->eps, c->nx, c->ny, c->cf,
+                                                                      c->d, c->w, c->dinv);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
@@ -316,7 +373,11 @@ pide_status launch_rhs_from_charge(pide_ctx* c, const double* rho, double* b, in
 }
 
 pide_status launch_lift(pide_ctx* c, const double* g, cudaStream_t st) {
-  lift_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(g, c->w, c->nx, c->ny, c->lift);
+  if (c->dims == 3)
+    lift3d_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(g, c->w, c->nx, c->ny, c->nz,
+                                                                    c->lift);
+  else
+    lift_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(g, c->w, c->nx, c->ny, c->lift);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
@@ -359,14 +420,17 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
   const uint32_t* fl = honor_done ? c->flags : nullptr;
   double* cm = c->colmax + col0;
   const int t = track ? 1 : 0;
-  if (emul && mode == 0 && R && !r_out && rfmt != RF_F64)
-    return launch_residual_df(c, b, u, B, lift, rfmt, R, c->ld,
-                              rfmt == RF_E4M3 ? c->col_scale + col0 : nullptr, cm, track, fl, st);
+  if (emul && mode == 0 && R && !r_out && rfmt != RF_F64) {
+    const pide_status s = launch_residual_df(c, b, u, B, lift, rfmt, R, c->ld,
+                                             rfmt == RF_E4M3 ? c->col_scale + col0 : nullptr, cm,
+                                             track, fl, st);
+    if (s != PIDE_EUNSUPPORTED) return s;      // else: the FP64 stencil below
+  }
   switch (rfmt) {
-    case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
+    case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -384,10 +448,10 @@ pide_status launch_residual_persistent(pide_ctx* c, const double* b, const doubl
   const int grid = c->num_sms * c->resid_ctas_per_sm;
   const float* cs = c->col_scale + col0;
   switch (rfmt) {
-    case RF_F32: residual_flat_kernel<RF_F32><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
-    case RF_BF16: residual_flat_kernel<RF_BF16><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
-    case RF_E4M3: residual_flat_kernel<RF_E4M3><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, cs, c->flags); break;
-    default: residual_flat_kernel<RF_F64><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_F32: residual_flat_kernel<RF_F32><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_BF16: residual_flat_kernel<RF_BF16><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_E4M3: residual_flat_kernel<RF_E4M3><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, cs, c->flags); break;
+    default: residual_flat_kernel<RF_F64><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -482,11 +546,13 @@ pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, i
   ProfScope ps(c, st, 1);
   dim3 g = col_grid(c->n, B);
   double* raw = c->colmax + 2 * (size_t)c->ws_B;
-  if (emul && mode == 0) {
-    PIDE_TRY(launch_residual_df(c, b, u, B, lift, RF_F32, c->Rf, c->ld, nullptr, raw, true,
-                                c->flags, st));
-  } else {
-    residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv,
+  pide_status sdf = PIDE_EUNSUPPORTED;
+  if (emul && mode == 0)
+    sdf = launch_residual_df(c, b, u, B, lift, RF_F32, c->Rf, c->ld, nullptr, raw, true, c->flags,
+                             st);
+  if (sdf != PIDE_OK && sdf != PIDE_EUNSUPPORTED) return sdf;
+  if (sdf == PIDE_EUNSUPPORTED) {
+    residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv,
                                                lift, c->Rf, nullptr, nullptr, raw, 1, c->flags);
   }
   PIDE_CUDA_TRY(cudaGetLastError());
@@ -507,7 +573,7 @@ pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int
   b += (size_t)col0 * c->n;
   if (u) u += (size_t)col0 * c->n;
   if (from_residual) {
-    residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, c->ld, mode, c->w, c->dinv, lift,
+    residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift,
                                                nullptr, nullptr, nullptr, raw, 1, c->flags);
   } else {
     colmax_raw_prep_kernel<<<g, 256, 0, st>>>(b, c->n, mode, c->dinv, lift, raw);

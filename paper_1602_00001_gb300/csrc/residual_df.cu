@@ -101,13 +101,15 @@ __device__ __noinline__ double residual_node_fp64(const double* __restrict__ bc,
                                                   const double* __restrict__ uc,
                                                   const double* __restrict__ w4,
                                                   const double* __restrict__ lift, int n, int mx,
-                                                  int p) {
-  const int c = p % mx;
+                                                  int plane, int p) {
+  const int c = p % mx, pp = p % plane;
   double r = lift ? bc[p] + (lift[p] - uc[p]) : bc[p] - uc[p];
   if (c > 0) r = fma(w4[p], uc[p - 1], r);
   if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
-  if (p >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
-  if (p + mx < n) r = fma(w4[3 * n + p], uc[p + mx], r);
+  if (pp >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
+  if (pp + mx < plane) r = fma(w4[3 * n + p], uc[p + mx], r);
+  if (p >= plane) r = fma(w4[4 * (size_t)n + p], uc[p - plane], r);
+  if (p + plane < n) r = fma(w4[5 * (size_t)n + p], uc[p + plane], r);
   return r;
 }
 
@@ -138,21 +140,26 @@ __device__ __forceinline__ void store_r(void* R, size_t idx, float s, float e, f
 }
 
 // Weights of the residual split into float pairs; zero toward boundary
-// neighbours (their values enter through the lift).  wh[p] = (W, E, S, N).
-__global__ void wsplit_kernel(const double* __restrict__ w4, int n, int mx,
-                              float4* __restrict__ wh, float4* __restrict__ wl) {
+// neighbours (their values enter through the lift).  wh[p] = (W, E, S, N),
+// wl[p] the low parts, and for a 3-D grid wz[p] = (D hi, U hi, D lo, U lo).
+__global__ void wsplit_kernel(const double* __restrict__ w4, int n, int mx, int plane,
+                              float4* __restrict__ wh, float4* __restrict__ wl,
+                              float4* __restrict__ wz) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int c = p % mx;
-    const double w[4] = {c > 0 ? w4[p] : 0.0, c < mx - 1 ? w4[n + p] : 0.0,
-                         p >= mx ? w4[2 * n + p] : 0.0, p + mx < n ? w4[3 * n + p] : 0.0};
-    float h[4], l[4];
+    const int c = p % mx, pp = p % plane;
+    const double w[6] = {c > 0 ? w4[p] : 0.0, c < mx - 1 ? w4[n + p] : 0.0,
+                         pp >= mx ? w4[2 * n + p] : 0.0, pp + mx < plane ? w4[3 * n + p] : 0.0,
+                         (wz && p >= plane) ? w4[4 * (size_t)n + p] : 0.0,
+                         (wz && p + plane < n) ? w4[5 * (size_t)n + p] : 0.0};
+    float h[6], l[6];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 6; ++k) {
       h[k] = __double2float_rn(w[k]);
       l[k] = __double2float_rn(w[k] - (double)h[k]);
     }
     wh[p] = make_float4(h[0], h[1], h[2], h[3]);
     wl[p] = make_float4(l[0], l[1], l[2], l[3]);
+    if (wz) wz[p] = make_float4(h[4], h[5], l[4], l[5]);
   }
 }
 
@@ -160,6 +167,7 @@ __global__ void wsplit_kernel(const double* __restrict__ w4, int n, int mx,
 // nodes per thread, a tile of 256 * SM_NR nodes per block.
 constexpr int SM_NRS[4] = {4, 8, 2, 4};
 constexpr size_t SMEM_MAX = 48 * 1024;   // larger halos (very wide grids) take the register kernel
+constexpr size_t SMEM_MAX_3D = 200 * 1024;  // 3-D halos (one z-plane each side), opt-in shared memory
 
 __device__ __forceinline__ int clampi(int q, int n) { return q < 0 ? 0 : (q >= n ? n - 1 : q); }
 
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(256, 2) residual_df_reg_kernel(
           s = __fadd_rn(ah, al);
           e = __fsub_rn(al, __fsub_rn(s, ah));
         } else {
-          split_f64_slow(residual_node_fp64(bc, uc, w4, lift, n, mx, p), s, e);
+          split_f64_slow(residual_node_fp64(bc, uc, w4, lift, n, mx, n, p), s, e);
         }
         store_r<RF>(R, (size_t)col * ldr + p, s, e, isc[cc]);
         if (track) mxr[cc] = fmaxf(mxr[cc], fabsf(s));
@@ -309,20 +317,21 @@ __device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float wh, float 
 // on zeros and not stored.  The fast route needs max(|f_p|, |u_p|) >= 2^-60
 // and a finite result (a value at or above 2^128 is staged as NaN); other
 // nodes take the FP64 route.
-template <int RF, int SM_NR>
+template <int RF, int SM_NR, bool DIM3>
 __global__ void __launch_bounds__(256) residual_df_kernel(
-    const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int B, int ldr,
-    const float4* __restrict__ wh4, const float4* __restrict__ wl4,
-    const double* __restrict__ w4, const double* __restrict__ lift, void* __restrict__ R,
-    const float* __restrict__ col_scale, double* __restrict__ colmax_r, int track,
-    const uint32_t* __restrict__ flags) {
+    const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int plane, int B,
+    int ldr, const float4* __restrict__ wh4, const float4* __restrict__ wl4,
+    const float4* __restrict__ wz4, const double* __restrict__ w4,
+    const double* __restrict__ lift, void* __restrict__ R, const float* __restrict__ col_scale,
+    double* __restrict__ colmax_r, int track, const uint32_t* __restrict__ flags) {
   extern __shared__ float4 su[];   // [L]
   __shared__ float red[2][8];
   if (flags && flags[FLAG_DONE]) return;
   constexpr int T = 256 * SM_NR;
-  const int L = T + 2 * mx + 2;
+  const int halo = DIM3 ? plane : mx;   // farthest neighbour: one z-plane (3-D) or one row (2-D)
+  const int L = T + 2 * halo + 2;
   const int P0 = blockIdx.x * T;
-  const int q0 = P0 - mx - 1;
+  const int q0 = P0 - halo - 1;
   const int ca = 2 * blockIdx.y, cb = ca + 1;
   const bool has_b = cb < B;
   const double* ua = u + (size_t)ca * n;
@@ -362,18 +371,24 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
     df_fma2(ah, al, wh.y, -wh.y, -wl.y, make_float2(ce.x, ce.y), make_float2(ce.z, ce.w));
     df_fma2(ah, al, wh.z, -wh.z, -wl.z, make_float2(cs.x, cs.y), make_float2(cs.z, cs.w));
     df_fma2(ah, al, wh.w, -wh.w, -wl.w, make_float2(cn.x, cn.y), make_float2(cn.z, cn.w));
+    if (DIM3) {
+      const float4 wz = wz4[p];
+      const float4 cd = su[i - plane], cu = su[i + plane];
+      df_fma2(ah, al, wz.x, -wz.x, -wz.z, make_float2(cd.x, cd.y), make_float2(cd.z, cd.w));
+      df_fma2(ah, al, wz.y, -wz.y, -wz.w, make_float2(cu.x, cu.y), make_float2(cu.z, cu.w));
+    }
     const float2 s = __fadd2_rn(ah, al);
     const float2 e = sub2(al, sub2(s, ah));
     float sa = s.x, ea = e.x, sb = s.y, eb = e.y;
     if (!(fmaxf(fmaxf(fabsf(c0.x), fabsf(bha)), fabsf(lh)) >= 0x1p-60f) ||
         !(fabsf(sa) <= 3.4028234e38f))
-      split_f64_slow(residual_node_fp64(ba, ua, w4, lift, n, mx, p), sa, ea);
+      split_f64_slow(residual_node_fp64(ba, ua, w4, lift, n, mx, DIM3 ? plane : n, p), sa, ea);
     store_r<RF>(R, (size_t)ca * ldr + p, sa, ea, isa);
     if (track) mxa = fmaxf(mxa, fabsf(sa));
     if (has_b) {
       if (!(fmaxf(fmaxf(fabsf(c0.y), fabsf(bhb)), fabsf(lh)) >= 0x1p-60f) ||
           !(fabsf(sb) <= 3.4028234e38f))
-        split_f64_slow(residual_node_fp64(bb, ub, w4, lift, n, mx, p), sb, eb);
+        split_f64_slow(residual_node_fp64(bb, ub, w4, lift, n, mx, DIM3 ? plane : n, p), sb, eb);
       store_r<RF>(R, (size_t)cb * ldr + p, sb, eb, isb);
       if (track) mxb = fmaxf(mxb, fabsf(sb));
     }
@@ -465,24 +480,48 @@ __global__ void prep_df_bf16_kernel(const double* __restrict__ b, int n, int ldr
 
 pide_status launch_wsplit(pide_ctx* c, cudaStream_t st) {
   const int g = (c->n + 255) / 256 < c->num_sms * 8 ? (c->n + 255) / 256 : c->num_sms * 8;
-  wsplit_kernel<<<g > 0 ? g : 1, 256, 0, st>>>(c->w, c->n, c->mx, c->wsp, c->wsp + c->n);
+  wsplit_kernel<<<g > 0 ? g : 1, 256, 0, st>>>(c->w, c->n, c->mx, plane_of(c), c->wsp,
+                                               c->wsp + c->n,
+                                               c->dims == 3 ? c->wsp + 2 * (size_t)c->n : nullptr);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
 
-template <int NR>
-static void launch_df_smem(pide_ctx* c, const double* b, const double* u, int B,
-                           const double* lift, int rfmt, void* R, int ldr, const float* col_scale,
-                           double* colmax_r, int t, const uint32_t* flags, size_t smem,
-                           cudaStream_t st) {
+template <int NR, bool DIM3>
+static pide_status launch_df_smem(pide_ctx* c, const double* b, const double* u, int B,
+                                  const double* lift, int rfmt, void* R, int ldr,
+                                  const float* col_scale, double* colmax_r, int t,
+                                  const uint32_t* flags, size_t smem, cudaStream_t st) {
   const dim3 g((c->n + 256 * NR - 1) / (256 * NR), (B + 1) / 2, 1);
   const float4* wh = c->wsp;
   const float4* wl = c->wsp + c->n;
+  const float4* wz = DIM3 ? c->wsp + 2 * (size_t)c->n : nullptr;
+  const int plane = plane_of(c);
   switch (rfmt) {
-    case RF_BF16: residual_df_kernel<RF_BF16, NR><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    case RF_F32: residual_df_kernel<RF_F32, NR><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    default: residual_df_kernel<RF_E4M3, NR><<<g, 256, smem, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    case RF_BF16: {
+      auto k = residual_df_kernel<RF_BF16, NR, DIM3>;
+      if (smem > 48 * 1024)
+        PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags);
+      break;
+    }
+    case RF_F32: {
+      auto k = residual_df_kernel<RF_F32, NR, DIM3>;
+      if (smem > 48 * 1024)
+        PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags);
+      break;
+    }
+    default: {
+      auto k = residual_df_kernel<RF_E4M3, NR, DIM3>;
+      if (smem > 48 * 1024)
+        PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags);
+      break;
+    }
   }
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
 }
 
 pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, int B,
@@ -493,25 +532,35 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   if (rfmt != RF_BF16 && rfmt != RF_F32 && rfmt != RF_E4M3) return PIDE_EINVAL;
   const int t = track ? 1 : 0;
   const int nr = SM_NRS[c->resid_shape & 3];
-  const size_t smem = (256 * (size_t)nr + 2 * (size_t)c->mx + 2) * sizeof(float4);
+  const bool three = c->dims == 3;
+  const size_t halo = three ? (size_t)plane_of(c) : (size_t)c->mx;
+  const size_t smem = (256 * (size_t)nr + 2 * halo + 2) * sizeof(float4);
+  if (three) {
+    // a z-plane of halo on each side; beyond SMEM_MAX_3D the caller uses the FP64 stencil
+    if (smem > SMEM_MAX_3D) return PIDE_EUNSUPPORTED;
+    switch (nr) {
+      case 8: return launch_df_smem<8, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
+      case 2: return launch_df_smem<2, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
+      default: return launch_df_smem<4, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
+    }
+  }
   if (smem <= SMEM_MAX) {
     switch (nr) {
-      case 8: launch_df_smem<8>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
-      case 2: launch_df_smem<2>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
-      default: launch_df_smem<4>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st); break;
+      case 8: return launch_df_smem<8, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
+      case 2: return launch_df_smem<2, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
+      default: return launch_df_smem<4, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
     }
-  } else {
-    constexpr int NR = 4, COLS = 2;
-    int gx = (c->n + 256 * NR - 1) / (256 * NR);
-    if (gx > 1024) gx = 1024;
-    const dim3 g(gx, (B + COLS - 1) / COLS, 1);
-    const float4* wh = c->wsp;
-    const float4* wl = c->wsp + c->n;
-    switch (rfmt) {
-      case RF_BF16: residual_df_reg_kernel<RF_BF16, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-      case RF_F32: residual_df_reg_kernel<RF_F32, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-      default: residual_df_reg_kernel<RF_E4M3, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
-    }
+  }
+  constexpr int NR = 4, COLS = 2;
+  int gx = (c->n + 256 * NR - 1) / (256 * NR);
+  if (gx > 1024) gx = 1024;
+  const dim3 g(gx, (B + COLS - 1) / COLS, 1);
+  const float4* wh = c->wsp;
+  const float4* wl = c->wsp + c->n;
+  switch (rfmt) {
+    case RF_BF16: residual_df_reg_kernel<RF_BF16, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    case RF_F32: residual_df_reg_kernel<RF_F32, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    default: residual_df_reg_kernel<RF_E4M3, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
