@@ -616,6 +616,23 @@ def main():
         2 * 2 * (((n + 127) // 128) * (((n + 127) // 128) + 1) // 2) * 128 * 128
     b1_gbs = b1_bytes * b1_apply_launches / (b1_apply_ms * 1e-3) / 1e9
 
+    # ---- the other batch sizes of the metric's definition (B = 64, 4096), same sweeps:
+    #      B = 64 columns of the batch; B = 4096 the batch four times over
+    batch_sweep = {}
+    if NN == NODES and B == BATCH:
+        for Bx in (64, 4096):
+            bx = b[:Bx].contiguous() if Bx <= B else b.repeat((Bx + B - 1) // B, 1)[:Bx].contiguous()
+            ux = torch.empty_like(bx)
+            s.reserve(Bx)
+            msx = timed(lambda: s.apply(bx, ux, sweeps=k), 5)
+            ex = float(((ux[:min(Bx, len(sample_cols))] - u[:min(Bx, len(sample_cols))]).abs()
+                        .amax(dim=1) / u[:min(Bx, len(sample_cols))].abs().amax(dim=1)).max())
+            batch_sweep[str(Bx)] = {"value": world * Bx / (msx * 1e-3), "unit": UNIT,
+                                    "ms_per_step": msx, "sweeps": k,
+                                    "max_rel_diff_vs_b1024_columns": ex}
+            del bx, ux
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI from pinned host memory, copies inside the timed
     #      region: pide_solve_stream over E_BATCHES steps of B columns (each step's input
     #      copied in and its solution copied out, overlapping the neighbouring steps' solves)
@@ -700,6 +717,7 @@ def main():
                      "avg_launch_ms": gemm_ms, "launches": apply_launches,
                      "algorithmic_flops_per_launch": flops_total / max(apply_launches, 1)},
         "kernel_ms_per_step": {c: prof[c][1] / args.steps for c in prof},
+        "other_batch_sizes": batch_sweep,
         "overlap": bool(s.get_tuning()["overlap"]),
         "tuning": s.get_tuning(),
         "gpu_launches": launches,
