@@ -38,22 +38,140 @@ struct BatchProb {
   int rbf16;              // 1: R holds BF16 for the grouped tensor-core apply, 0: FP32
 };
 
-constexpr int BT = 64;   // rows and columns per tile item
-constexpr int BK = 32;   // K step
+// SIMT apply of the FP32 (and non-tensor-core BF16) problems.  An item is
+// (problem, row tile, column tile, shape): the tile holds SB_OUT = 8192 outputs
+// as TM x TN with TN = 16, 32 or 64 columns (the smallest that covers the
+// problem's B, so small batches waste no lanes) and TM = 8192 / TN rows.
+// 256 threads, each 8 rows x 4 columns; K in steps of 16, double-buffered in
+// shared memory; A read as 16-byte vectors (4 FP32 or 4 BF16 entries).
+constexpr int SB_K = 16;
+constexpr int SB_OUT = 8192;
+constexpr int SB_TMMAX = 512;
+constexpr int SB_APAD = SB_TMMAX + 4;
+constexpr int SB_XPAD = 64 + 4;
+constexpr size_t SB_SMEM = (size_t)(2 * SB_K * SB_APAD + 2 * SB_K * SB_XPAD) * sizeof(float);
 
-__device__ __forceinline__ float load_a(const BatchProb& P, size_t idx) {
-  if (P.fmt == 0) return reinterpret_cast<const float*>(P.inv)[idx];
-  return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(P.inv)[idx]);
+__device__ __forceinline__ int sb_tn(int code) { return code == 0 ? 16 : (code == 1 ? 32 : 64); }
+
+// four consecutive entries of row gp from column gk (gk a multiple of 4; zero past n)
+__device__ __forceinline__ float4 load_a4(const BatchProb& P, int gp, int gk) {
+  if (gp >= P.n || gk >= P.n) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const size_t idx = (size_t)gp * P.ld + gk;
+  if (gk + 3 < P.n) {
+    if (P.fmt == 0) return *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(P.inv) + idx);
+    const uint2 raw = *reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(P.inv) + idx);
+    return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xFFFF0000u),
+                       __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xFFFF0000u));
+  }
+  float v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = gk + j;
+    v[j] = k < P.n ? (P.fmt == 0 ? reinterpret_cast<const float*>(P.inv)[idx + j]
+                                 : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(P.inv)[idx + j]))
+                   : 0.f;
+  }
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// four consecutive entries of right-hand side gc from row gk (zero past n or past B)
+__device__ __forceinline__ float4 load_x4(const BatchProb& P, int gc, bool col_ok, int gk) {
+  if (!col_ok || gk >= P.n) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* src = P.R + (size_t)gc * P.ld + gk;
+  if (gk + 3 < P.n) return *reinterpret_cast<const float4*>(src);
+  return make_float4(src[0], gk + 1 < P.n ? src[1] : 0.f, gk + 2 < P.n ? src[2] : 0.f, 0.f);
+}
+
+template <int TN>
+__device__ __forceinline__ void simt_tile(const BatchProb& P, int p0, int c0, int accumulate,
+                                          float* __restrict__ sA, float* __restrict__ sX) {
+  constexpr int TM = SB_OUT / TN;
+  constexpr int CG = TN / 4;             // column groups of 4
+  constexpr int AL = TM / 64;            // float4 loads of A per thread and K step
+  const int t = threadIdx.x;
+  const int cg = t % CG, rg = t / CG;    // this thread: rows rg*8 .. +7, columns cg*4 .. +3
+  const int ncols = min(TN, P.B - c0);
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float4 ra[AL], rx = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool xloader = t < TN * 4;
+  const int xc = t >> 2, xk = (t & 3) * 4;
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < AL; ++q) {
+      const int e = t + 256 * q;
+      ra[q] = load_a4(P, p0 + (e >> 2), k0 + (e & 3) * 4);
+    }
+    if (xloader) rx = load_x4(P, c0 + xc, xc < ncols, k0 + xk);
+  };
+  auto store = [&](int buf) {
+    float* A = sA + buf * SB_K * SB_APAD;
+#pragma unroll
+    for (int q = 0; q < AL; ++q) {
+      const int e = t + 256 * q;
+      const int r = e >> 2, k = (e & 3) * 4;
+      A[(k + 0) * SB_APAD + r] = ra[q].x;
+      A[(k + 1) * SB_APAD + r] = ra[q].y;
+      A[(k + 2) * SB_APAD + r] = ra[q].z;
+      A[(k + 3) * SB_APAD + r] = ra[q].w;
+    }
+    if (xloader) {
+      float* X = sX + buf * SB_K * SB_XPAD;
+      X[(xk + 0) * SB_XPAD + xc] = rx.x;
+      X[(xk + 1) * SB_XPAD + xc] = rx.y;
+      X[(xk + 2) * SB_XPAD + xc] = rx.z;
+      X[(xk + 3) * SB_XPAD + xc] = rx.w;
+    }
+  };
+  const int nk = (P.n + SB_K - 1) / SB_K;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int ks = 0; ks < nk; ++ks) {
+    const int buf = ks & 1;
+    if (ks + 1 < nk) load((ks + 1) * SB_K);
+    const float* A = sA + buf * SB_K * SB_APAD + rg * 8;
+    const float* X = sX + buf * SB_K * SB_XPAD + cg * 4;
+#pragma unroll
+    for (int kk = 0; kk < SB_K; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(A + kk * SB_APAD);
+      const float4 a1 = *reinterpret_cast<const float4*>(A + kk * SB_APAD + 4);
+      const float4 x = *reinterpret_cast<const float4*>(X + kk * SB_XPAD);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+    }
+    if (ks + 1 < nk) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cg * 4 + j;
+    if (c >= ncols) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int p = p0 + rg * 8 + i;
+      if (p >= P.n) continue;
+      double* dst = P.u + (size_t)(c0 + c) * P.n + p;
+      *dst = accumulate ? *dst + (double)acc[i][j] : (double)acc[i][j];
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __restrict__ probs,
                                                             const int4* __restrict__ items,
                                                             int nitems, int* __restrict__ counter,
                                                             int accumulate, int phase) {
-  __shared__ float As[BK][BT + 4];
-  __shared__ float Xs[BK][BT + 4];
+  extern __shared__ float sb_smem[];
+  float* sA = sb_smem;
+  float* sX = sb_smem + 2 * SB_K * SB_APAD;
   __shared__ int s_item;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
@@ -63,55 +181,11 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
     const int4 w = items[it];
     const BatchProb P = probs[w.x];
     if (phase > P.pad) continue;                      // this problem already ran its sweeps
-    const int p0 = w.y * BT, c0 = w.z * BT;
-    const int ncols = min(BT, P.B - c0);
-    const bool active = ty * 4 < ncols;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < P.n; k0 += BK) {
-#pragma unroll
-      for (int q = 0; q < (BT * BK) / 256; ++q) {
-        const int e = threadIdx.x + 256 * q;
-        const int r = e / BK, kk = e % BK;
-        const int gk = k0 + kk;
-        const int gp = p0 + r, gc = c0 + r;
-        As[kk][r] = (gp < P.n && gk < P.n) ? load_a(P, (size_t)gp * P.ld + gk) : 0.f;
-        Xs[kk][r] = (r < ncols && gk < P.n) ? P.R[(size_t)gc * P.ld + gk] : 0.f;
-      }
-      __syncthreads();
-      if (active) {
-#pragma unroll 8
-        for (int kk = 0; kk < BK; ++kk) {
-          float av[4], xv[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) xv[j] = Xs[kk][ty * 4 + j];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
-        }
-      }
-      __syncthreads();
-    }
-    if (active) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = ty * 4 + j;
-        if (c >= ncols) continue;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int p = p0 + tx + 16 * i;
-          if (p >= P.n) continue;
-          double* dst = P.u + (size_t)(c0 + c) * P.n + p;
-          *dst = accumulate ? *dst + (double)acc[i][j] : (double)acc[i][j];
-        }
-      }
-    }
+    const int tn = sb_tn(w.w);
+    const int p0 = w.y * (SB_OUT / tn), c0 = w.z * tn;
+    if (w.w == 0) simt_tile<16>(P, p0, c0, accumulate, sA, sX);
+    else if (w.w == 1) simt_tile<32>(P, p0, c0, accumulate, sA, sX);
+    else simt_tile<64>(P, p0, c0, accumulate, sA, sX);
   }
 }
 
@@ -388,7 +462,7 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
     }
   pide_batch* p = new pide_batch();
   std::vector<BatchProb> probs(nprob);
-  struct Item { int prob, mt, ct; double cost; };
+  struct Item { int prob, mt, ct; double cost; int shape = 0; };
   std::vector<Item> items, gitems;
   std::vector<GroupProb> gprobs;
   std::vector<int> gindex(nprob, -1);
@@ -443,13 +517,13 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
       const int mt = (h->n + 127) / 128, ct = (Bs[k] + GBN - 1) / GBN;
       for (int i = 0; i < mt; ++i)
         for (int j = 0; j < ct; ++j) gitems.push_back({gindex[k], i, j, (double)g.num_kb});
-    } else {
-      const int mt = (h->n + BT - 1) / BT, ct = (Bs[k] + BT - 1) / BT;
+    } else if (Bs[k] > 0) {
+      // SIMT: the narrowest tile shape that covers B (16, 32 or 64 columns)
+      const int code = Bs[k] <= 16 ? 0 : (Bs[k] <= 32 ? 1 : 2);
+      const int tn = code == 0 ? 16 : (code == 1 ? 32 : 64), tm = SB_OUT / tn;
+      const int mt = (h->n + tm - 1) / tm, ct = (Bs[k] + tn - 1) / tn;
       for (int i = 0; i < mt; ++i)
-        for (int j = 0; j < ct; ++j) {
-          const int cols = std::min(BT, Bs[k] - j * BT);
-          items.push_back({k, i, j, (double)h->n * ((cols + 3) / 4)});
-        }
+        for (int j = 0; j < ct; ++j) items.push_back({k, i, j, (double)h->n * tm * tn, code});
     }
     for (int c = 0; c < Bs[k]; ++c) colitems.push_back(make_int2(k, c));
     p->hs.push_back(h);
@@ -460,7 +534,7 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
   std::stable_sort(items.begin(), items.end(),
                    [](const Item& a, const Item& c) { return a.cost > c.cost; });
   std::vector<int4> it4(items.size());
-  for (size_t i = 0; i < items.size(); ++i) it4[i] = make_int4(items[i].prob, items[i].mt, items[i].ct, 0);
+  for (size_t i = 0; i < items.size(); ++i) it4[i] = make_int4(items[i].prob, items[i].mt, items[i].ct, items[i].shape);
   std::stable_sort(gitems.begin(), gitems.end(),
                    [](const Item& a, const Item& c) { return a.cost > c.cost; });
   std::vector<int4> g4(gitems.size());
@@ -499,9 +573,11 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
 
 static pide_status batch_apply(pide_batch* p, int phase, cudaStream_t st) {
   if (p->nitems > 0) {
-    const int grid_apply = std::min(p->nitems, p->num_sms * 4);
-    batched_apply_kernel<<<grid_apply, 256, 0, st>>>(p->d_probs, p->d_items, p->nitems,
-                                                     p->d_counter + phase, phase > 0, phase);
+    const int grid_apply = std::min(p->nitems, p->num_sms * 2);
+    PIDE_CUDA_TRY(cudaFuncSetAttribute(batched_apply_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM));
+    batched_apply_kernel<<<grid_apply, 256, SB_SMEM, st>>>(p->d_probs, p->d_items, p->nitems,
+                                                           p->d_counter + phase, phase > 0, phase);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
   if (p->ngitems > 0) {
