@@ -193,3 +193,55 @@ def residual(nx: int, ny: int, nz: int, eps: np.ndarray | None, b: np.ndarray,
         lo, hi = max(0, -c), min(n, n - c)
         Lu[:, lo:hi] += band[lo:hi, w + c] * U[:, lo + c:hi + c]
     return np.atleast_2d(b) - Lu
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (not in the paper; the same derivation as the 2-D oracle's)
+# ---------------------------------------------------------------------------
+
+
+def adjoint_gradients(nx: int, ny: int, nz: int, eps: np.ndarray, b: np.ndarray,
+                      gout: np.ndarray):
+    """Gradients of Loss(u), u = L(eps)^-1 b with b held fixed and zero
+    boundary values: mu = S^-1 gout (S = D L symmetric), dLoss/db = D mu, and
+    for a face of permittivity e_f between nodes p and q
+        dLoss/de_f = mu_p b_p + mu_q b_q - (mu_p - mu_q)(u_p - u_q)
+    (a boundary node contributes mu = 0, no b term, u = 0), chained to the
+    node values through d e_f / d eps_a = 2 eps_b^2 / (eps_a + eps_b)^2.
+    Returns (u, dLoss/db, dLoss/deps[nz][ny][nx])."""
+    eps = _eps(nx, ny, nz, eps)
+    _, S, d = interior_operator(nx, ny, nz, eps)
+    b2 = np.atleast_2d(b)
+    G = np.atleast_2d(gout)
+    u = (np.linalg.solve(S, (b2 * d[None, :]).T)).T          # L u = b  <=>  S u = D b
+    mu = np.linalg.solve(S, G.T).T
+    db = mu * d[None, :]
+    deps = np.zeros((nz, ny, nx))
+
+    def val(arr, l, i, j, c):
+        return arr[c, interior_index(l, i, j, nx, ny)]
+
+    for l in range(nz):
+        for i in range(ny):
+            for j in range(nx):
+                for dz, dy, dx in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):   # each face once
+                    l2, i2, j2 = l + dz, i + dy, j + dx
+                    if l2 >= nz or i2 >= ny or j2 >= nx:
+                        continue
+                    ba = is_boundary(l, i, j, nx, ny, nz)
+                    bb = is_boundary(l2, i2, j2, nx, ny, nz)
+                    if ba and bb:
+                        continue
+                    tot = 0.0
+                    for c in range(b2.shape[0]):
+                        mu_a = 0.0 if ba else val(mu, l, i, j, c)
+                        mu_b = 0.0 if bb else val(mu, l2, i2, j2, c)
+                        u_a = 0.0 if ba else val(u, l, i, j, c)
+                        u_b = 0.0 if bb else val(u, l2, i2, j2, c)
+                        b_a = 0.0 if ba else val(b2, l, i, j, c)
+                        b_b = 0.0 if bb else val(b2, l2, i2, j2, c)
+                        tot += mu_a * b_a + mu_b * b_b - (mu_a - mu_b) * (u_a - u_b)
+                    ea, eb = eps[l, i, j], eps[l2, i2, j2]
+                    deps[l, i, j] += tot * 2 * eb * eb / (ea + eb) ** 2
+                    deps[l2, i2, j2] += tot * 2 * ea * ea / (ea + eb) ** 2
+    return u, db, deps

@@ -135,3 +135,38 @@ def test_second_order_convergence():
         return np.max(np.abs(un - u[1:-1, 1:-1, 1:-1].reshape(-1))) / np.max(np.abs(u))
     e1, e2 = err(9), err(17)
     assert 3.5 <= e1 / e2 <= 4.6, (e1, e2)
+
+
+def test_adjoint_against_central_differences():
+    """dLoss/db and dLoss/deps of Loss = 0.5 ||u - u_t||^2, u = L(eps)^-1 b,
+    against FP64 central differences of the oracle's own solve."""
+    nx, ny, nz = 5, 4, 5
+    eps = _lognormal(nx, ny, nz, 11)
+    rng = np.random.default_rng(12)
+    n = (nx - 2) * (ny - 2) * (nz - 2)
+    b = rng.standard_normal((2, n))
+    ut = rng.standard_normal((2, n))
+
+    def loss(e, bb):
+        u = O3.solve(nx, ny, nz, e, bb, route="dense")
+        return 0.5 * np.sum((u - ut) ** 2)
+
+    u0 = O3.solve(nx, ny, nz, eps, b, route="dense")
+    u, db, deps = O3.adjoint_gradients(nx, ny, nz, eps, b, u0 - ut)
+    assert np.max(np.abs(u - u0)) < 1e-13 * np.max(np.abs(u0))
+    for l in range(nz):
+        for i in range(ny):
+            for j in range(nx):
+                st = 1e-6 * eps[l, i, j]
+                ep, em = eps.copy(), eps.copy()
+                ep[l, i, j] += st
+                em[l, i, j] -= st
+                fd = (loss(ep, b) - loss(em, b)) / (2 * st)
+                assert abs(fd - deps[l, i, j]) <= 1e-6 * max(1.0, abs(fd)), (l, i, j, fd, deps[l, i, j])
+    for c in range(2):
+        for p in range(0, n, 2):
+            bp, bm = b.copy(), b.copy()
+            bp[c, p] += 1e-6
+            bm[c, p] -= 1e-6
+            fd = (loss(eps, bp) - loss(eps, bm)) / 2e-6
+            assert abs(fd - db[c, p]) <= 1e-6 * max(1.0, abs(fd))
