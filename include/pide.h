@@ -132,8 +132,9 @@ pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precisio
  * (z, y, x).  The handle serves pide_apply, pide_apply_host, pide_solve_stream,
  * pide_residual, pide_rhs_from_charge (b = -h^2 rho / d with the six-face d),
  * boundary values g [nz][ny][nx] in pide_apply, the tuning and profiling
- * hooks, and pide_apply_backward without dLoss/deps.  pide_save, the batched
- * plans and pide_apply_noalloc return PIDE_EUNSUPPORTED for it.  The FP64
+ * hooks, pide_apply_backward (six-face dLoss/deps, deps_dev [nz][ny][nx]) and
+ * pide_save / pide_load.  The batched plans and pide_apply_noalloc return
+ * PIDE_EUNSUPPORTED for it.  The FP64
  * inverse is formed by block elimination over z-planes: setup cost grows as
  * ((nx-2)(ny-2))^3 (nz-2) on GB300's FP64 pipe (seconds at 32^3 unknowns).
  */

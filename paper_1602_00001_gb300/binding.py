@@ -336,9 +336,22 @@ class Solver:
         # grid shape is in the file header; read it back from the header bytes
         import struct
         with open(path, "rb") as f:
-            head = f.read(8 + 4 * 6 + 8)
-        _, _, nx, ny, prec, n, ld = struct.unpack("<8s6i", head[:32])
+            head = f.read(56 + 8)
+        _, version, nx, ny, prec, n, ld = struct.unpack("<8s6i", head[:32])
         (h,) = struct.unpack("<d", head[32:40])
+        if version == 2:                          # 3-D: nz follows the 56-byte header
+            (nz, _dims) = struct.unpack("<2i", head[56:64])
+            obj = Solver3D.__new__(Solver3D)
+            import torch
+            obj.lib = lib
+            obj.nx, obj.ny, obj.nz, obj.h = nx, ny, nz, h
+            obj.n = (nx - 2) * (ny - 2) * (nz - 2)
+            obj.precision = inv[hi.precision]
+            obj.device = torch.device("cuda", torch.cuda.current_device())
+            obj.handle = h_out
+            obj.eps = None
+            obj._eps_keep = None
+            return obj
         return cls(nx, ny, h, None, inv[hi.precision], _handle=h_out)
 
     @contextmanager

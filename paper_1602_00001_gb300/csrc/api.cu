@@ -641,10 +641,6 @@ extern "C" pide_status pide_apply_backward(pide_handle h, const double* gout_dev
     set_error("pide_apply_backward: b_dev is required");
     return PIDE_EINVAL;
   }
-  if (h->dims == 3 && deps_dev) {
-    set_error("pide_apply_backward: dLoss/deps is built for 2-D grids only (pass deps_dev = NULL)");
-    return PIDE_EUNSUPPORTED;
-  }
   if (B == 0) return PIDE_OK;
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -695,6 +691,11 @@ struct FileHeader {
   uint64_t store_bytes;
 };
 
+// Version 2 (3-D grids) follows the header with this block.
+struct FileHeader3 {
+  int32_t nz, dims;
+};
+
 uint64_t fnv1a(const void* data, size_t len) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
   uint64_t hsh = 1469598103934665603ull;
@@ -711,10 +712,6 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
     set_error("pide_save: bad argument");
     return PIDE_EINVAL;
   }
-  if (h->dims == 3) {
-    set_error("pide_save: the file format holds 2-D grids only");
-    return PIDE_EUNSUPPORTED;
-  }
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
   PIDE_CUDA_TRY(cudaDeviceSynchronize());
   FILE* f = std::fopen(path, "wb");
@@ -726,7 +723,7 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
                             (h->prec == PIDE_FP64 ? 8 : h->prec == PIDE_FP32 ? 4 : h->prec == PIDE_BF16 ? 2 : 1);
   FileHeader hd{};
   std::memcpy(hd.magic, "PIDEINV1", 8);
-  hd.version = 1;
+  hd.version = h->dims == 3 ? 2 : 1;
   hd.nx = h->nx;
   hd.ny = h->ny;
   hd.prec = (int)h->prec;
@@ -736,6 +733,10 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
   hd.eps_hash = fnv1a(h->eps_host.data(), h->eps_host.size() * sizeof(double));
   hd.store_bytes = main_bytes;
   bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  if (hd.version == 2) {
+    const FileHeader3 h3{h->nz, h->dims};
+    ok = ok && std::fwrite(&h3, sizeof(h3), 1, f) == 1;
+  }
   ok = ok && std::fwrite(h->eps_host.data(), sizeof(double), h->eps_host.size(), f) == h->eps_host.size();
   std::vector<char> buf(1 << 26);
   auto dump = [&](const void* dev, size_t bytes) {
@@ -770,14 +771,17 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   }
   FileHeader hd{};
   bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, "PIDEINV1", 8) == 0 &&
-            hd.version == 1;
+            (hd.version == 1 || hd.version == 2);
+  FileHeader3 h3{1, 2};
+  if (ok && hd.version == 2) ok = std::fread(&h3, sizeof(h3), 1, f) == 1 && h3.dims == 3;
   pide_grid g{hd.nx, hd.ny, hd.h};
-  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 4) {
+  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 4 || h3.nz < 1 ||
+      (h3.dims == 3 && (h3.nz < 3 || (int64_t)(hd.nx - 2) * (hd.ny - 2) * (h3.nz - 2) >= (int64_t)1 << 30))) {
     std::fclose(f);
     set_error(std::string(path) + ": not a pide inverse file");
     return PIDE_EINVAL;
   }
-  std::vector<double> eps((size_t)hd.nx * hd.ny);
+  std::vector<double> eps((size_t)hd.nx * hd.ny * (h3.dims == 3 ? h3.nz : 1));
   ok = std::fread(eps.data(), sizeof(double), eps.size(), f) == eps.size();
   if (!ok || fnv1a(eps.data(), eps.size() * sizeof(double)) != hd.eps_hash) {
     std::fclose(f);
@@ -787,7 +791,7 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
   c->prec = (pide_precision)hd.prec;
-  pide_status s = setup_operator(c, g.nx, g.ny, 1, g.h, 2, eps.data(), st);
+  pide_status s = setup_operator(c, g.nx, g.ny, h3.nz, g.h, h3.dims, eps.data(), st);
   if (s == PIDE_OK && (c->n != hd.n || c->ld != hd.ld)) {
     set_error("pide_load: header sizes do not match the grid");
     s = PIDE_EINVAL;

@@ -333,6 +333,41 @@ __global__ void face_grad_kernel(const double* __restrict__ mu, const double* __
   }
 }
 
+// The same on an nx x ny x nz node grid: six faces per node.
+__global__ void face_grad3d_kernel(const double* __restrict__ mu, const double* __restrict__ u,
+                                   const double* __restrict__ b, const double* __restrict__ eps,
+                                   int nx, int ny, int nz, int B, double* __restrict__ deps) {
+  const int mx = nx - 2, my = ny - 2, mz = nz - 2, n = mx * my * mz;
+  const int N = nx * ny * nz;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N;
+       node += gridDim.x * blockDim.x) {
+    const int j = node % nx, i = (node / nx) % ny, l = node / (nx * ny);
+    const bool in_a = (l > 0 && l < nz - 1 && i > 0 && i < ny - 1 && j > 0 && j < nx - 1);
+    const int pa = in_a ? ((l - 1) * my + (i - 1)) * mx + (j - 1) : -1;
+    const double ea = eps[node];
+    double acc = 0.0;
+    const int dl[6] = {0, 0, 0, 0, -1, 1}, di[6] = {0, 0, -1, 1, 0, 0}, dj[6] = {-1, 1, 0, 0, 0, 0};
+    for (int k = 0; k < 6; ++k) {
+      const int l2 = l + dl[k], i2 = i + di[k], j2 = j + dj[k];
+      if (l2 < 0 || l2 >= nz || i2 < 0 || i2 >= ny || j2 < 0 || j2 >= nx) continue;
+      const bool in_b = (l2 > 0 && l2 < nz - 1 && i2 > 0 && i2 < ny - 1 && j2 > 0 && j2 < nx - 1);
+      if (!in_a && !in_b) continue;
+      const int pb = in_b ? ((l2 - 1) * my + (i2 - 1)) * mx + (j2 - 1) : -1;
+      double T = 0.0;
+      for (int c = 0; c < B; ++c) {
+        const size_t o = (size_t)c * n;
+        const double mua = in_a ? mu[o + pa] : 0.0, mub = in_b ? mu[o + pb] : 0.0;
+        const double ua = in_a ? u[o + pa] : 0.0, ub = in_b ? u[o + pb] : 0.0;
+        const double ba = in_a ? b[o + pa] : 0.0, bb = in_b ? b[o + pb] : 0.0;
+        T += mua * ba + mub * bb - (mua - mub) * (ua - ub);
+      }
+      const double eb = eps[((size_t)l2 * ny + i2) * nx + j2];
+      acc += T * 2.0 * eb * eb / ((ea + eb) * (ea + eb));
+    }
+    deps[node] += acc;
+  }
+}
+
 __global__ void scale_d_kernel(const double* __restrict__ mu, const double* __restrict__ d,
                                double* __restrict__ out, int n, long long total) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
@@ -476,9 +511,13 @@ pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const
 pide_status launch_face_grad(pide_ctx* c, const double* mu, const double* u, const double* b,
                              int B, double* deps, cudaStream_t st) {
   ProfScope ps(c, st, 3);
-  const int N = c->nx * c->ny;
-  face_grad_kernel<<<grid_for(N, 128, c->num_sms), 128, 0, st>>>(mu, u, b, c->eps, c->nx, c->ny,
-                                                                 B, deps);
+  const int N = c->nx * c->ny * c->nz;
+  if (c->dims == 3)
+    face_grad3d_kernel<<<grid_for(N, 128, c->num_sms), 128, 0, st>>>(mu, u, b, c->eps, c->nx,
+                                                                     c->ny, c->nz, B, deps);
+  else
+    face_grad_kernel<<<grid_for(N, 128, c->num_sms), 128, 0, st>>>(mu, u, b, c->eps, c->nx, c->ny,
+                                                                   B, deps);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }

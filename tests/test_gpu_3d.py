@@ -128,19 +128,41 @@ def test_stream_and_charge():
     assert _rel(u[[0, 255, 256, 699]], ref) < 1e-6
 
 
-def test_unsupported_operations():
-    from paper_1602_00001_gb300.binding import PideError, apply_batched
-    nx, ny, nz = 6, 5, 4
-    s = _solver(nx, ny, nz, None, "bf16")
+def test_adjoint_3d():
+    """dLoss/db and dLoss/deps over the six faces against the 3-D oracle's
+    adjoint (itself pinned by central differences)."""
+    nx, ny, nz = 7, 6, 8
+    eps = _eps(nx, ny, nz, 13)
+    n = (nx - 2) * (ny - 2) * (nz - 2)
+    rng = np.random.default_rng(14)
+    b = rng.standard_normal((3, n))
+    ut = rng.standard_normal((3, n))
+    u_o, db_o, deps_o = O3.adjoint_gradients(nx, ny, nz, eps, b, np.zeros_like(b))
+    u_o, db_o, deps_o = O3.adjoint_gradients(nx, ny, nz, eps, b, u_o - ut)
+    for prec, sweeps, tol in (("fp64", 0, 1e-11), ("bf16", 6, 1e-6)):
+        s = _solver(nx, ny, nz, eps, prec)
+        u = s.apply(b, sweeps=sweeps)
+        db, deps = s.backward(u - torch.from_numpy(ut).cuda(), u, torch.from_numpy(b).cuda(),
+                              sweeps=sweeps)
+        assert deps.shape == (nz, ny, nx)
+        assert _rel(db.cpu().numpy(), db_o) < tol
+        assert _rel(deps.cpu().numpy(), deps_o) < tol
+
+
+def test_save_load_and_unsupported(tmp_path):
+    from paper_1602_00001_gb300.binding import PideError, Solver, apply_batched
+    nx, ny, nz = 6, 5, 7
+    eps = _eps(nx, ny, nz, 15)
+    s = _solver(nx, ny, nz, eps, "bf16")
+    rng = np.random.default_rng(16)
+    b = rng.standard_normal((40, s.n))
+    u1 = s.apply(b, sweeps=5).cpu().numpy()
+    path = str(tmp_path / "inv3d.bin")
+    s.save(path)
+    s2 = Solver.load(path)
+    assert s2.nz == nz and s2.n == s.n and s2.info().dims == 3
+    u2 = s2.apply(b, sweeps=5).cpu().numpy()
+    assert _rel(u2, u1) < 1e-12
+    bb = torch.zeros((2, s.n), dtype=torch.float64, device="cuda")
     with pytest.raises(PideError):
-        s.save("/tmp/pide3d_should_not_exist.bin")
-    n = s.n
-    b = torch.zeros((2, n), dtype=torch.float64, device="cuda")
-    u = torch.zeros_like(b)
-    with pytest.raises(PideError):
-        apply_batched([s], [b], [u])
-    # the adjoint solve itself works in 3-D; dLoss/deps does not
-    db, _ = s.backward(torch.ones_like(b), b, b, sweeps=2, want_deps=False)
-    assert torch.isfinite(db).all()
-    with pytest.raises(PideError):
-        s.backward(torch.ones_like(b), b, b, sweeps=2)
+        apply_batched([s], [bb], [torch.zeros_like(bb)])
