@@ -582,11 +582,33 @@ extern "C" pide_status pide_solve_stream(pide_handle h, const double* in_host, d
   PIDE_CUDA_TRY(cudaEventRecord(fork, st));
   PIDE_CUDA_TRY(cudaStreamWaitEvent(h->cstream, fork, 0));
   PIDE_CUDA_TRY(cudaStreamWaitEvent(h->dstream, fork, 0));
-  const int64_t nchunks = (T + cols - 1) / cols;
+  // Chunk schedule: a quarter chunk first and last, so that only a small copy
+  // is exposed at each end (the first input copy precedes every solve, the last
+  // output copy follows them); full chunks between.
+  std::vector<std::pair<int64_t, int>> chunks;
+  if (T <= cols) {
+    chunks.emplace_back(0, (int)T);
+  } else {
+    const int r = cols / 4 > 0 ? cols / 4 : 1;
+    chunks.emplace_back(0, r);
+    int64_t c0 = r, rest = T - r;
+    while (rest > (int64_t)cols + r) {
+      chunks.emplace_back(c0, cols);
+      c0 += cols;
+      rest -= cols;
+    }
+    if (rest > r) {
+      chunks.emplace_back(c0, (int)(rest - r));
+      chunks.emplace_back(c0 + rest - r, r);
+    } else {
+      chunks.emplace_back(c0, (int)rest);
+    }
+  }
+  const int64_t nchunks = (int64_t)chunks.size();
   for (int64_t i = 0; i < nchunks; ++i) {
     const int q = (int)(i & 1);
-    const int64_t c0 = i * cols;
-    const int nc = (int)((T - c0) < cols ? (T - c0) : cols);
+    const int64_t c0 = chunks[i].first;
+    const int nc = chunks[i].second;
     const size_t off = (size_t)c0 * h->n, bytes = (size_t)nc * h->n * sizeof(double);
     double* din = h->sbuf_in + q * slot;
     double* dout = h->sbuf_out + q * slot;
