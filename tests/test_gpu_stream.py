@@ -36,7 +36,11 @@ def _setup(T, seed):
 
 @pytest.mark.parametrize("T,chunk", [(2500, 1024), (700, 1024), (5, 2), (3, 1)])
 def test_stream_equals_chunked_device_apply(T, chunk):
-    """Ragged last chunk, a single chunk, odd chunks, one column per chunk."""
+    """Ragged last chunk, a single chunk, odd chunks, one column per chunk.
+    The driver cuts the sequence into its own pieces (a quarter chunk first
+    and last), so a column may go through another apply kernel than in a
+    device apply of `chunk` columns: the two refined results agree to the
+    refinement's accuracy, and both to the oracle's."""
     nx, ny, h, eps, rho = _setup(T, 40)
     b = O.rhs_from_charge(nx, ny, h, eps, rho)
     s = _solver(nx, ny, h, eps, "bf16")
@@ -44,7 +48,7 @@ def test_stream_equals_chunked_device_apply(T, chunk):
     for c0 in range(0, T, chunk):
         ud = s.apply(b[c0:c0 + chunk], sweeps=4).cpu().numpy()
         d = np.abs(u[c0:c0 + chunk] - ud).max(axis=1) / np.abs(ud).max(axis=1)
-        assert d.max() <= 1e-12, (c0, float(d.max()))
+        assert d.max() <= 1e-7, (c0, float(d.max()))
     cols = [0, T // 2, T - 1]
     ref = O.solve(nx, ny, eps, b[cols], route="band")
     assert O.rel_error_eq6(u[cols], ref) < 1e-6
