@@ -185,7 +185,7 @@ pide_status pide_apply_host(pide_handle h, const double* b_host, double* u_host,
  * first use, 4 * chunk * n * 8 bytes, kept for later calls): the copy of
  * chunk i + 1 to the device and of chunk i - 1 to the host run on internal
  * streams under the refined solve of chunk i (max_sweeps refinement sweeps,
- * fixed count).  When T > chunk the first and the last piece are a quarter
+ * fixed count).  When T > chunk the first and the last piece are a half
  * chunk, so that little copy time is left outside the solves.  Pinned host memory is needed for the copies to overlap.
  * Ordered after the work already on `stream`; returns after synchronising.
  * in_host and u_host must not overlap.

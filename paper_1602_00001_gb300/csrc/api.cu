@@ -582,14 +582,14 @@ extern "C" pide_status pide_solve_stream(pide_handle h, const double* in_host, d
   PIDE_CUDA_TRY(cudaEventRecord(fork, st));
   PIDE_CUDA_TRY(cudaStreamWaitEvent(h->cstream, fork, 0));
   PIDE_CUDA_TRY(cudaStreamWaitEvent(h->dstream, fork, 0));
-  // Chunk schedule: a quarter chunk first and last, so that only a small copy
+  // Chunk schedule: a half chunk first and last, so that only a smaller copy
   // is exposed at each end (the first input copy precedes every solve, the last
   // output copy follows them); full chunks between.
   std::vector<std::pair<int64_t, int>> chunks;
   if (T <= cols) {
     chunks.emplace_back(0, (int)T);
   } else {
-    const int r = cols / 4 > 0 ? cols / 4 : 1;
+    const int r = cols / 2 > 0 ? cols / 2 : 1;
     chunks.emplace_back(0, r);
     int64_t c0 = r, rest = T - r;
     while (rest > (int64_t)cols + r) {

@@ -37,7 +37,7 @@ def _setup(T, seed):
 @pytest.mark.parametrize("T,chunk", [(2500, 1024), (700, 1024), (5, 2), (3, 1)])
 def test_stream_equals_chunked_device_apply(T, chunk):
     """Ragged last chunk, a single chunk, odd chunks, one column per chunk.
-    The driver cuts the sequence into its own pieces (a quarter chunk first
+    The driver cuts the sequence into its own pieces (a half chunk first
     and last), so a column may go through another apply kernel than in a
     device apply of `chunk` columns: the two refined results agree to the
     refinement's accuracy, and both to the oracle's."""
