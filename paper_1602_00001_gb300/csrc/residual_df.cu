@@ -165,7 +165,7 @@ __global__ void wsplit_kernel(const double* __restrict__ w4, int n, int mx, int 
 
 // Launch shapes of the shared-memory kernel (PIDE_TUNE_RESID_SHAPE): SM_NR
 // nodes per thread, a tile of 256 * SM_NR nodes per block.
-constexpr int SM_NRS[4] = {4, 8, 2, 4};
+constexpr int SM_NRS[4] = {4, 8, 2, 16};
 constexpr size_t SMEM_MAX = 48 * 1024;   // larger halos (very wide grids) take the register kernel
 constexpr size_t SMEM_MAX_3D = 200 * 1024;  // 3-D halos (one z-plane each side), opt-in shared memory
 
@@ -531,14 +531,17 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   if (B == 0) return PIDE_OK;
   if (rfmt != RF_BF16 && rfmt != RF_F32 && rfmt != RF_E4M3) return PIDE_EINVAL;
   const int t = track ? 1 : 0;
-  const int nr = SM_NRS[c->resid_shape & 3];
   const bool three = c->dims == 3;
+  // default (-1): 8 nodes per thread in 2-D; 16 in 3-D, where the halo is a
+  // whole z-plane on each side and a longer tile stages relatively less of it
+  const int nr = c->resid_shape < 0 ? (three ? 16 : 8) : SM_NRS[c->resid_shape & 3];
   const size_t halo = three ? (size_t)plane_of(c) : (size_t)c->mx;
   const size_t smem = (256 * (size_t)nr + 2 * halo + 2) * sizeof(float4);
   if (three) {
     // a z-plane of halo on each side; beyond SMEM_MAX_3D the caller uses the FP64 stencil
     if (smem > SMEM_MAX_3D) return PIDE_EUNSUPPORTED;
     switch (nr) {
+      case 16: return launch_df_smem<16, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
       case 8: return launch_df_smem<8, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
       case 2: return launch_df_smem<2, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
       default: return launch_df_smem<4, true>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
@@ -546,6 +549,7 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   }
   if (smem <= SMEM_MAX) {
     switch (nr) {
+      case 16: return launch_df_smem<16, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
       case 8: return launch_df_smem<8, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
       case 2: return launch_df_smem<2, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);
       default: return launch_df_smem<4, false>(c, b, u, B, lift, rfmt, R, ldr, col_scale, colmax_r, t, flags, smem, st);

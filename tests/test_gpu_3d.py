@@ -74,7 +74,8 @@ def _df_bound(nx, ny, nz, eps, f, u, r_exact):
     return 2.0 ** -23 * np.abs(r_exact) + 2.0 ** -42 * sc + 2.0 ** -149
 
 
-@pytest.mark.parametrize("dims,shape", [((10, 9, 8), 0), ((10, 9, 8), 1), ((26, 26, 4), 1)])
+@pytest.mark.parametrize("dims,shape", [((10, 9, 8), 0), ((10, 9, 8), 1), ((10, 9, 8), 3),
+                                        ((10, 9, 8), -1), ((26, 26, 4), 1)])
 def test_double_float_residual(dims, shape):
     """The refinement's residual kernel with a z-plane of halo on each side;
     (26, 26, 4) with 8 nodes per thread needs more than 48 KB of shared
