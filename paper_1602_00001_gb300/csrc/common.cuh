@@ -116,7 +116,7 @@ struct pide_ctx {
   int gemv_unroll = 8;              // 16-byte loads in flight per lane: 4 or 8
   int symv = 1;                     // B = 1 through the packed symmetric S^-1 (half the bytes)
   int resid_emul = 1;               // refinement residual in double-float (off the FP64 pipe)
-  int resid_shape = -1;             // its launch shape: -1 auto (8 nodes per thread 2-D, 16 3-D); 0..3: 4, 8, 2, 16
+  int resid_shape = -1;             // its launch shape: -1 default (8 nodes per thread); 0..3: 4, 8, 2, 16
   // profiling
   bool prof_on = false;
   struct Ev { cudaEvent_t a, b; int cls; };
