@@ -6,10 +6,12 @@ events on the launching stream and keeps the fastest.  Results live in a JSON
 cache keyed by GPU name (path: $PIDE_TUNE_CACHE, default
 ~/.cache/pide_tune.json) so later processes reuse them without timing.
 
-Knobs: GEMM tile width (128/256) and stream-K tail (on/off) for B > 128;
-GEMV block size (256..1024) and loads in flight (4/8) for B = 1; the largest
-B sent to the GEMV instead of the tensor-core GEMM (1..8).  The knobs change
-only the launch shape, never the arithmetic beyond FP32 summation order.
+Knobs: for B > 128 the SM-pair GEMM (256 x 256 tiles) against the single-SM
+one (tile width 128/256), the stream-K tail (on/off) and the L2 policy of the
+streamed inverse; GEMV block size (256..1024) and loads in flight (4/8) for
+B = 1; the largest B sent to the GEMV instead of the tensor-core GEMM (1..8).
+The knobs change only the launch shape, never the arithmetic beyond FP32
+summation order.
 """
 from __future__ import annotations
 
@@ -61,8 +63,12 @@ def candidates(B: int):
         for sk in (0, 1):
             yield {"gemv_max_b": 1, "gemm_streamk": sk}
     else:
+        for sk, hint in itertools.product([0, 1], [0, 1]):
+            yield {"gemv_max_b": 1, "gemm_2cta": 1, "gemm_bn": 256, "gemm_streamk": sk,
+                   "gemm_a_hint": hint}
         for bn, sk in itertools.product([128, 256], [0, 1]):
-            yield {"gemv_max_b": 1, "gemm_bn": bn, "gemm_streamk": sk}
+            yield {"gemv_max_b": 1, "gemm_2cta": 0, "gemm_bn": bn, "gemm_streamk": sk,
+                   "gemm_a_hint": 0}
 
 
 class TuneCache:

@@ -38,7 +38,8 @@ def test_candidates_are_valid_knobs(B):
     c = list(T.candidates(B))
     assert c
     for k in c:
-        assert set(k) <= {"gemv_max_b", "gemv_threads", "gemv_unroll", "gemm_bn", "gemm_streamk"}
+        assert set(k) <= {"gemv_max_b", "gemv_threads", "gemv_unroll", "gemm_bn", "gemm_streamk",
+                          "gemm_2cta", "gemm_a_hint"}
 
 
 def test_tune_picks_fastest_and_caches(tmp_path):
