@@ -309,8 +309,9 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_GEMV_UNROLL   16-byte loads in flight per lane: 4 or 8 (default 8)
  *   PIDE_TUNE_GEMV_MAX_B    largest B served by the GEMV instead of the GEMM: 1..8 (default 1)
  *   PIDE_TUNE_GEMM_BN       tensor-core tile width for B > 128: 128 or 256 (default 256)
- *   PIDE_TUNE_GEMM_STREAMK  1: split the last partial wave of tiles over all SMs by
- *                           k-blocks (FP64 atomic partial sums); 0: whole tiles only
+ *   PIDE_TUNE_GEMM_STREAMK  1 (default): split the last partial wave of tiles over all SMs by
+ *                           k-blocks (FP64 atomic partial sums) -- on SM pairs only when
+ *                           there are fewer than four full waves; 0: whole tiles only
  *   PIDE_TUNE_OVERLAP       1: for B >= 512 with tol <= 0, split the columns in
  *                           two groups and run each group's FP64 residual on a
  *                           low-priority internal stream under the other group's

@@ -422,8 +422,13 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const int n_tiles = (B + BN2 - 1) / BN2;
   const int tiles = m_tiles * n_tiles;
   const int num_kb = (c->n + (MODE ? 128 : 64) - 1) / (MODE ? 128 : 64);
+  // The stream-K tail pays only when the data-parallel waves are few: at 198^2,
+  // B = 1024 (8.1 waves) it measured the same time as whole tiles but 1.3-1.5 GB
+  // more DRAM reads per launch; at B = 256 (2.0 waves) whole tiles would idle
+  // half the pairs for a third of the launch.
+  const bool few_waves = tiles < 4 * G;
   int clusters, dp_tiles;
-  if (!c->gemm_streamk || tiles % G == 0 || n_tiles > G) {
+  if (!c->gemm_streamk || !few_waves || tiles % G == 0 || n_tiles > G) {
     clusters = tiles < G ? tiles : G;
     dp_tiles = tiles;
   } else {
