@@ -106,3 +106,21 @@ def test_pair_full_size_sampled():
     b_np = b[cols[:2]].cpu().numpy()
     ref = O.solve(nx, ny, eps, b_np, route="band")
     assert O.rel_error_eq6(u2[cols[:2]].cpu().numpy(), ref) < 1e-6
+
+
+def test_pair_stream_k_at_full_size():
+    """198^2 unknowns, B = 256: 154 pair tiles on the resident pairs (about two
+    waves), where the pair kernel takes the stream-K tail; against whole tiles."""
+    nx = ny = 200
+    h = 1.0 / 199
+    eps = W.eps_fourier(nx, ny, h, seed=1)
+    rho = W.moving_charges(nx, ny, h, seed=6, steps=256)
+    s = _solver(nx, ny, h, eps, "bf16")
+    b = s.rhs_from_charge(torch.from_numpy(rho).cuda())
+    s.set_tuning(gemm_streamk=1)
+    u1 = s.apply(b, sweeps=0)
+    s.set_tuning(gemm_streamk=0)
+    u0 = s.apply(b, sweeps=0)
+    # the same FP32 sums in another order: bounded by the contraction of |Q| |R|
+    d = ((u1 - u0).abs().amax(dim=1) / u0.abs().amax(dim=1)).max().item()
+    assert d < 1e-4, d
