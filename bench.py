@@ -37,7 +37,7 @@ WORKLOAD = "198^2 interior (200x200 nodes), Fourier-field eps, 16 moving charges
 # DRAM traffic (read + write) of one launch of the GEMM at this workload, from the
 # one-pass ncu capture summarised in profiles/gemm_tc2_bf16_198sq_b1024.md; valid
 # only for the kernel source it was taken on (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh).
-GEMM_TRAFFIC = {"sha1": "5f2e27f05c72b6a64fb9ab6e1651ea9daa0892c9", "bytes": 6.509e9,
+GEMM_TRAFFIC = {"sha1": "ea420f939bc9db9d92b770dc969407b1ab7f7233", "bytes": 4.94e9,
                 "precision": "bf16", "batch": 1024, "nodes": 200}
 
 
