@@ -644,13 +644,14 @@ def main():
     u_host = torch.empty((E_BATCHES * B, n), dtype=torch.float64).pin_memory()
     s.solve_stream(in_host, u_host, chunk=B, sweeps=k)          # allocates the device slots
     torch.cuda.synchronize()
-    e2e_calls = 2
-    t0 = time.perf_counter()
-    for _ in range(e2e_calls):
+    # three timed calls; the median call is reported, every call's rate beside it
+    call_rates = []
+    for _ in range(3):
+        t0 = time.perf_counter()
         s.solve_stream(in_host, u_host, chunk=B, sweeps=k)
-    e2e_s = (time.perf_counter() - t0) / (e2e_calls * E_BATCHES)
-    e2e_s = reduce_max(e2e_s, dist)
-    e2e_value = world * B / e2e_s
+        dt = reduce_max((time.perf_counter() - t0) / E_BATCHES, dist)
+        call_rates.append(world * B / dt)
+    e2e_value = sorted(call_rates)[1]
     ud = u[sample_cols].cpu()
     e2e_err = float(((u_host[(E_BATCHES - 1) * B:][sample_cols] - ud).abs().amax(dim=1)
                      / ud.abs().amax(dim=1)).max())
@@ -724,6 +725,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * 8,
                 "d2h_bytes_per_step": B * n * 8,
                 "api": f"pide_solve_stream, {E_BATCHES} steps of B={B} per call, pinned host buffers",
+                "calls": call_rates, "reported": "median of the calls",
                 "max_rel_diff_vs_device_apply": e2e_err,
                 "apply_host_one_batch_per_call": ah_value},
     }
