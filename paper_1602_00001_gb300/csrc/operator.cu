@@ -198,7 +198,8 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
   const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
   double mxr = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int c = p % mx, pp = p % plane;   // x, and the index inside a z-plane
+    const int c = p % mx;
+    const int pp = plane == n ? p : p % plane;   // index inside a z-plane (2-D: the whole grid)
     double r;
     if (mode == 1) r = fma(bc[p], dinv[p], -uc[p]);
     else if (lift) r = bc[p] + (lift[p] - uc[p]);
@@ -237,7 +238,8 @@ __global__ void residual_flat_kernel(const double* __restrict__ b, const double*
        k += (long long)gridDim.x * blockDim.x) {
     const int col = (int)(k / n);
     const int p = (int)(k - (long long)col * n);
-    const int c = p % mx, pp = p % plane;
+    const int c = p % mx;
+    const int pp = plane == n ? p : p % plane;
     const double* uc = u + (size_t)col * n;
     // streaming loads (evict-first): keep the concurrent GEMM's operands in L2
     const double bp = __ldcs(b + k);

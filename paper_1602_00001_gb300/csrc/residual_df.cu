@@ -102,7 +102,7 @@ __device__ __noinline__ double residual_node_fp64(const double* __restrict__ bc,
                                                   const double* __restrict__ w4,
                                                   const double* __restrict__ lift, int n, int mx,
                                                   int plane, int p) {
-  const int c = p % mx, pp = p % plane;
+  const int c = p % mx, pp = plane == n ? p : p % plane;
   double r = lift ? bc[p] + (lift[p] - uc[p]) : bc[p] - uc[p];
   if (c > 0) r = fma(w4[p], uc[p - 1], r);
   if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
