@@ -182,7 +182,7 @@ __global__ void prep_kernel(const double* __restrict__ b, int n, int ldr, int mo
 //   r = f - L u = f - u_p + sum_q w_pq u_q   (interior neighbours q only)
 // with f as in prep.  Written quantised to R (the next apply's right side),
 // optionally in full to r_out, and its column max |r| into colmax_r.
-template <int RF>
+template <int RF, bool DIM3>
 __global__ void residual_kernel(const double* __restrict__ b, const double* __restrict__ u,
                                 int n, int mx, int plane, int ldr, int mode,
                                 const double* __restrict__ w4,
@@ -199,7 +199,7 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
   double mxr = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int c = p % mx;
-    const int pp = plane == n ? p : p % plane;   // index inside a z-plane (2-D: the whole grid)
+    const int pp = DIM3 ? p % plane : p;   // index inside a z-plane (2-D: the whole grid)
     double r;
     if (mode == 1) r = fma(bc[p], dinv[p], -uc[p]);
     else if (lift) r = bc[p] + (lift[p] - uc[p]);
@@ -208,8 +208,10 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
     if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
     if (pp >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
     if (pp + mx < plane) r = fma(w4[3 * n + p], uc[p + mx], r);
-    if (p >= plane) r = fma(w4[4 * (size_t)n + p], uc[p - plane], r);          // 3-D only
-    if (p + plane < n) r = fma(w4[5 * (size_t)n + p], uc[p + plane], r);
+    if (DIM3) {
+      if (p >= plane) r = fma(w4[4 * (size_t)n + p], uc[p - plane], r);
+      if (p + plane < n) r = fma(w4[5 * (size_t)n + p], uc[p + plane], r);
+    }
     if (R) store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
     if (r_out) r_out[(size_t)col * n + p] = r;
     if (track) mxr = fmax(mxr, fabs(r));
@@ -224,7 +226,7 @@ __global__ void residual_kernel(const double* __restrict__ b, const double* __re
 // grid: used under a concurrently running tensor-core apply, where a full-size
 // grid would crowd the SMs' warp schedulers that the GEMM's single-thread TMA
 // and MMA issuers depend on.
-template <int RF>
+template <int RF, bool DIM3>
 __global__ void residual_flat_kernel(const double* __restrict__ b, const double* __restrict__ u,
                                      int n, int mx, int plane, int B, int ldr, int mode,
                                      const double* __restrict__ w4,
@@ -239,7 +241,7 @@ __global__ void residual_flat_kernel(const double* __restrict__ b, const double*
     const int col = (int)(k / n);
     const int p = (int)(k - (long long)col * n);
     const int c = p % mx;
-    const int pp = plane == n ? p : p % plane;
+    const int pp = DIM3 ? p % plane : p;
     const double* uc = u + (size_t)col * n;
     // streaming loads (evict-first): keep the concurrent GEMM's operands in L2
     const double bp = __ldcs(b + k);
@@ -252,8 +254,10 @@ __global__ void residual_flat_kernel(const double* __restrict__ b, const double*
     if (c < mx - 1) r = fma(w4[n + p], __ldcs(uc + p + 1), r);
     if (pp >= mx) r = fma(w4[2 * n + p], __ldcs(uc + p - mx), r);
     if (pp + mx < plane) r = fma(w4[3 * n + p], __ldcs(uc + p + mx), r);
-    if (p >= plane) r = fma(w4[4 * (size_t)n + p], __ldcs(uc + p - plane), r);
-    if (p + plane < n) r = fma(w4[5 * (size_t)n + p], __ldcs(uc + p + plane), r);
+    if (DIM3) {
+      if (p >= plane) r = fma(w4[4 * (size_t)n + p], __ldcs(uc + p - plane), r);
+      if (p + plane < n) r = fma(w4[5 * (size_t)n + p], __ldcs(uc + p + plane), r);
+    }
     const float isc = col_scale ? 1.0f / col_scale[col] : 1.0f;
     store_rhs<RF>(R, (size_t)col * ldr + p, r, isc);
   }
@@ -464,10 +468,10 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
     if (s != PIDE_EUNSUPPORTED) return s;      // else: the FP64 stencil below
   }
   switch (rfmt) {
-    case RF_F64: residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    case RF_F32: residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    case RF_BF16: residual_kernel<RF_BF16><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
-    default: residual_kernel<RF_E4M3><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
+    case RF_F64: (c->dims == 3 ? residual_kernel<RF_F64, true> : residual_kernel<RF_F64, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_F32: (c->dims == 3 ? residual_kernel<RF_F32, true> : residual_kernel<RF_F32, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_BF16: (c->dims == 3 ? residual_kernel<RF_BF16, true> : residual_kernel<RF_BF16, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    default: (c->dims == 3 ? residual_kernel<RF_E4M3, true> : residual_kernel<RF_E4M3, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -485,10 +489,10 @@ pide_status launch_residual_persistent(pide_ctx* c, const double* b, const doubl
   const int grid = c->num_sms * c->resid_ctas_per_sm;
   const float* cs = c->col_scale + col0;
   switch (rfmt) {
-    case RF_F32: residual_flat_kernel<RF_F32><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
-    case RF_BF16: residual_flat_kernel<RF_BF16><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
-    case RF_E4M3: residual_flat_kernel<RF_E4M3><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, cs, c->flags); break;
-    default: residual_flat_kernel<RF_F64><<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_F32: (c->dims == 3 ? residual_flat_kernel<RF_F32, true> : residual_flat_kernel<RF_F32, false>)<<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_BF16: (c->dims == 3 ? residual_flat_kernel<RF_BF16, true> : residual_flat_kernel<RF_BF16, false>)<<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
+    case RF_E4M3: (c->dims == 3 ? residual_flat_kernel<RF_E4M3, true> : residual_flat_kernel<RF_E4M3, false>)<<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, cs, c->flags); break;
+    default: (c->dims == 3 ? residual_flat_kernel<RF_F64, true> : residual_flat_kernel<RF_F64, false>)<<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
@@ -593,7 +597,7 @@ pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, i
                              st);
   if (sdf != PIDE_OK && sdf != PIDE_EUNSUPPORTED) return sdf;
   if (sdf == PIDE_EUNSUPPORTED) {
-    residual_kernel<RF_F32><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv,
+    (c->dims == 3 ? residual_kernel<RF_F32, true> : residual_kernel<RF_F32, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv,
                                                lift, c->Rf, nullptr, nullptr, raw, 1, c->flags);
   }
   PIDE_CUDA_TRY(cudaGetLastError());
@@ -614,7 +618,7 @@ pide_status launch_fp8_scales(pide_ctx* c, const double* b, const double* u, int
   b += (size_t)col0 * c->n;
   if (u) u += (size_t)col0 * c->n;
   if (from_residual) {
-    residual_kernel<RF_F64><<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift,
+    (c->dims == 3 ? residual_kernel<RF_F64, true> : residual_kernel<RF_F64, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift,
                                                nullptr, nullptr, nullptr, raw, 1, c->flags);
   } else {
     colmax_raw_prep_kernel<<<g, 256, 0, st>>>(b, c->n, mode, c->dinv, lift, raw);
