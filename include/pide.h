@@ -341,7 +341,11 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_GEMM_A_HINT   L2 policy of the tensor-core apply's loads of the stored inverse:
  *                           0 evict-first, 1 (default) evict-normal, 2 evict-last (measured
  *                           on the SM-pair kernel at 198^2, B = 1024: 6.9 GB of DRAM reads per
- *                           launch with evict-first, 4.8 GB with either other policy, same time) */
+ *                           launch with evict-first, 4.8 GB with either other policy, same time)
+ *   PIDE_TUNE_RESID_PREFETCH  the refinement residual's L2 prefetch distance, in column pairs:
+ *                           each block prefetches its tile of the pair that many pairs ahead
+ *                           (0 = none, up to 4096; default 4: the 2-D residual at 158^2 and
+ *                           198^2 unknowns, B = 1024, 12-15% faster, 3-D unchanged) */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -354,7 +358,8 @@ typedef enum {
   PIDE_TUNE_RESID_EMUL = 8,
   PIDE_TUNE_RESID_SHAPE = 9,
   PIDE_TUNE_GEMM_2CTA = 10,
-  PIDE_TUNE_GEMM_A_HINT = 11
+  PIDE_TUNE_GEMM_A_HINT = 11,
+  PIDE_TUNE_RESID_PREFETCH = 12
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

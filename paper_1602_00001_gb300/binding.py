@@ -292,7 +292,8 @@ class Solver:
     TUNE_KEYS = {"gemv_threads": 0, "gemv_unroll": 1, "gemv_max_b": 2, "gemm_bn": 3,
                  "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6, "symv": 7,
                  "resid_emul": 8, "resid_shape": 9,
-                 "gemm_2cta": 10, "gemm_a_hint": 11}
+                 "gemm_2cta": 10, "gemm_a_hint": 11,
+                 "resid_prefetch": 12}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

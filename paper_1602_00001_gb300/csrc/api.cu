@@ -960,6 +960,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value < 0 || value > 2) break;
       h->gemm_a_hint = value;
       return PIDE_OK;
+    case PIDE_TUNE_RESID_PREFETCH:
+      if (value < 0 || value > 4096) break;
+      h->resid_prefetch = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -983,6 +987,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_RESID_SHAPE: *value = h->resid_shape; return PIDE_OK;
     case PIDE_TUNE_GEMM_2CTA: *value = h->gemm_2cta; return PIDE_OK;
     case PIDE_TUNE_GEMM_A_HINT: *value = h->gemm_a_hint; return PIDE_OK;
+    case PIDE_TUNE_RESID_PREFETCH: *value = h->resid_prefetch; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

@@ -117,6 +117,7 @@ struct pide_ctx {
   int symv = 1;                     // B = 1 through the packed symmetric S^-1 (half the bytes)
   int resid_emul = 1;               // refinement residual in double-float (off the FP64 pipe)
   int resid_shape = -1;             // its launch shape: -1 default (8 nodes per thread); 0..3: 4, 8, 2, 16
+  int resid_prefetch = 4;           // its L2 prefetch distance in column pairs (0: none)
   // profiling
   bool prof_on = false;
   struct Ev { cudaEvent_t a, b; int cls; };

@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
     int ldr, const float4* __restrict__ wh4, const float4* __restrict__ wl4,
     const float4* __restrict__ wz4, const double* __restrict__ w4,
     const double* __restrict__ lift, void* __restrict__ R, const float* __restrict__ col_scale,
-    double* __restrict__ colmax_r, int track, const uint32_t* __restrict__ flags) {
+    double* __restrict__ colmax_r, int track, const uint32_t* __restrict__ flags, int pf) {
   extern __shared__ float4 su[];   // [L]
   __shared__ float red[2][8];
   if (flags && flags[FLAG_DONE]) return;
@@ -336,6 +336,23 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
   const bool has_b = cb < B;
   const double* ua = u + (size_t)ca * n;
   const double* ub = u + (size_t)(has_b ? cb : ca) * n;
+  if (pf > 0) {
+    // L2 prefetch of the same tile of the column pair pf pairs ahead (the
+    // blocks that will run a few rounds later), 128-byte lines, in bounds
+    const int fa = ca + 2 * pf;
+    if (fa < B) {
+      const int lo = q0 < 0 ? 0 : q0, hi = (q0 + L < n) ? q0 + L : n;
+      const int blo = P0, bhi = (P0 + T < n) ? P0 + T : n;
+      const int nu = (hi - lo + 15) / 16, nb = (bhi - blo + 15) / 16;
+      const int ncol = (fa + 1 < B) ? 2 : 1;
+      for (int i = threadIdx.x; i < ncol * (nu + nb); i += 256) {
+        const int col = fa + i / (nu + nb), j = i % (nu + nb);
+        const double* a = (j < nu) ? u + (size_t)col * n + lo + 16 * j
+                                   : b + (size_t)col * n + blo + 16 * (j - nu);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+      }
+    }
+  }
   for (int i = threadIdx.x; i < L; i += 256) {
     const int q = q0 + i;
     float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
@@ -502,21 +519,21 @@ static pide_status launch_df_smem(pide_ctx* c, const double* b, const double* u,
       auto k = residual_df_kernel<RF_BF16, NR, DIM3>;
       if (smem > 48 * 1024)
         PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags);
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
       break;
     }
     case RF_F32: {
       auto k = residual_df_kernel<RF_F32, NR, DIM3>;
       if (smem > 48 * 1024)
         PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags);
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
       break;
     }
     default: {
       auto k = residual_df_kernel<RF_E4M3, NR, DIM3>;
       if (smem > 48 * 1024)
         PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags);
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
       break;
     }
   }

@@ -69,6 +69,30 @@ def test_residual_df_near_solution(with_g, shape):
         assert np.max(np.abs(r64 - r_exact)) <= 1e-13 * np.max(np.abs(u))
 
 
+@pytest.mark.parametrize("pf", [0, 1, 3, 4, 1000])
+def test_residual_df_prefetch_distance_changes_no_bit(pf):
+    """The L2 prefetch of the tile pf column pairs ahead (7 columns: 4 pairs,
+    the last a single column; 3 prefetches that single column, 4 and 1000
+    nothing) moves no result bit."""
+    nx, ny = 77, 69
+    h = 1.0 / 76
+    eps = W.eps_lognormal(nx, ny, seed=24)
+    rng = np.random.default_rng(25)
+    b = O.rhs_from_charge(nx, ny, h, eps, W.gaussian_blobs(nx, ny, h, 26, batch=7))
+    ref = O.solve(nx, ny, eps, b)
+    u = ref * (1.0 + 1e-5 * rng.standard_normal(ref.shape))
+    s = _solver(nx, ny, h, eps, "bf16")
+    assert s.get_tuning()["resid_prefetch"] == 4            # the default
+    s.set_tuning(resid_prefetch=0)
+    r0 = s.residual_df(b, u).cpu().numpy()
+    s.set_tuning(resid_prefetch=pf)
+    r = s.residual_df(b, u).cpu().numpy()
+    assert np.array_equal(r, r0)
+    r_exact = O.residual(nx, ny, eps, b, u)
+    bound = _bound(nx, ny, eps, b, u, r_exact)
+    assert np.all(np.abs(r.astype(np.float64) - r_exact) <= bound)
+
+
 def test_residual_df_wide_grid_register_kernel():
     """A grid row longer than the shared-memory halo allows (1028 interior
     nodes per row): the register kernel, with clamped neighbour loads."""
