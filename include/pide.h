@@ -63,7 +63,13 @@ typedef enum {
   PIDE_FP32 = 1,   /* FP32 inverse, FP32 SIMT apply, FP64 refinement */
   PIDE_BF16 = 2,   /* BF16 inverse, tensor-core apply (FP32 accumulate), FP64 refinement */
   PIDE_FP8 = 3,    /* e4m3 inverse with per-row scales (single term; study only) */
-  PIDE_FP8X2 = 4   /* e4m3 hi + lo terms with per-row scales, FP8 tensor cores */
+  PIDE_FP8X2 = 4,  /* e4m3 hi + lo terms with per-row scales, FP8 tensor cores */
+  PIDE_BF16_FP8 = 5 /* BF16 inverse Q plus an e4m3 correction term C with its own per-row
+                       scales s_p: C = e4m3((L^-1 - Q) / s_p).  Every apply contracts Q on the
+                       BF16 tensor cores; the applies that PIDE_TUNE_CORR_MASK selects add
+                       s_p t_j (C e4m3(R / t_j)) on the FP8 tensor cores (t_j = max|R_j| / 448),
+                       which cuts that sweep's error by a further ~2^-4 (B = 2..65535 only:
+                       B = 1 and the batched entry points use Q alone) */
 } pide_precision;
 
 typedef struct {
@@ -97,7 +103,10 @@ typedef struct {
 
 /* Per-kernel-class event timing, recorded on the launching stream. */
 typedef struct {
-  int32_t launches[4];   /* [0] apply (GEMM/GEMV) [1] residual [2] rhs prep [3] other */
+  int32_t launches[4];   /* [0] apply (GEMM/GEMV) [1] residual [2] rhs prep (with the
+                            e4m3 copy of R for the correction term) [3] other: the
+                            correction term's FP8 GEMM, the tolerance check, the
+                            adjoint's face gradients */
   double ms[4];          /* summed CUDA-event time per class */
 } pide_profile;
 
@@ -292,7 +301,8 @@ pide_status pide_profile_begin(pide_handle h);
 pide_status pide_profile_end(pide_handle h, pide_profile* out);
 
 /* Copy row p of the stored inverse L^-1 (converted to float64, scales
- * applied) to host memory dst[n]: lets tests check individual entries. */
+ * applied; PIDE_BF16_FP8: Q + s_p C, exact) to host memory dst[n]: lets tests
+ * check individual entries. */
 pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* dst_host);
 
 /* Table 1's experiment: round every entry of the stored inverse of an FP64
@@ -345,7 +355,11 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_RESID_PREFETCH  the refinement residual's L2 prefetch distance, in column pairs:
  *                           each block prefetches its tile of the pair that many pairs ahead
  *                           (0 = none, up to 4096; default 4: the 2-D residual at 158^2 and
- *                           198^2 unknowns, B = 1024, 12-15% faster, 3-D unchanged) */
+ *                           198^2 unknowns, B = 1024, 12-15% faster, 3-D unchanged)
+ *   PIDE_TUNE_CORR_MASK       PIDE_BF16_FP8 handles: bit k set = apply k adds the e4m3
+ *                           correction term (bit 0: the first apply, bit k: refinement sweep k;
+ *                           0 .. 2^30 - 1; default 2, the first sweep: at 198^2 unknowns,
+ *                           B = 1024, two sweeps then reach ~2e-7 where BF16 alone needs four) */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -359,7 +373,8 @@ typedef enum {
   PIDE_TUNE_RESID_SHAPE = 9,
   PIDE_TUNE_GEMM_2CTA = 10,
   PIDE_TUNE_GEMM_A_HINT = 11,
-  PIDE_TUNE_RESID_PREFETCH = 12
+  PIDE_TUNE_RESID_PREFETCH = 12,
+  PIDE_TUNE_CORR_MASK = 13
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

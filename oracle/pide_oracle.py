@@ -519,3 +519,13 @@ def quantize_rows_e4m3(M: np.ndarray, two_terms: bool):
     hi = round_e4m3(round_fp32(x))
     lo = round_e4m3(round_fp32(x - hi)) if two_terms else np.zeros_like(hi)
     return s, hi, lo
+
+
+def quantize_bf16_correction(M: np.ndarray):
+    """The BF16 store with an e4m3 correction term, written out: Q = bf16(M);
+    D = M - Q (exact in FP64: Q holds the leading bits of M); per-row scale
+    s_p = float32(max_q |D_pq| / 448) (1 for a zero row); C = e4m3(float32(D / s)).
+    Returns (Q, s, C) with M ~ Q + s C."""
+    Q = round_bf16(M)
+    s, C, _ = quantize_rows_e4m3(M - Q, False)
+    return Q, s, C

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpide.so")
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8x2": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8x2": 4, "bf16_fp8": 5}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
           6: "EUNSUPPORTED"}
 
@@ -135,7 +135,9 @@ class Solver:
     """One operator (grid + node permittivity) with its stored inverse.
 
     ``precision``: 'fp64' (plain FP64 inverse and apply), 'fp32', 'bf16',
-    'fp8' or 'fp8x2' (low-precision inverse, FP64 refinement).
+    'fp8' or 'fp8x2' (low-precision inverse, FP64 refinement), or 'bf16_fp8'
+    (BF16 inverse plus an e4m3 correction term added in the sweeps that the
+    'corr_mask' tuning key selects).
     """
 
     def __init__(self, nx: int, ny: int, h: float, eps=None, precision: str = "bf16",
@@ -293,7 +295,7 @@ class Solver:
                  "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6, "symv": 7,
                  "resid_emul": 8, "resid_shape": 9,
                  "gemm_2cta": 10, "gemm_a_hint": 11,
-                 "resid_prefetch": 12}
+                 "resid_prefetch": 12, "corr_mask": 13}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

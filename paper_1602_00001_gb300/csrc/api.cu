@@ -105,6 +105,9 @@ pide_status make_tma_maps(pide_ctx* c) {
   } else {
     return PIDE_OK;
   }
+  if (c->corr)
+    PIDE_TRY(encode_2d(&c->tmA_corr, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->corr, c->n, c->n,
+                       (uint64_t)c->ld, 128, 128));
   c->tmA_ok = true;
   return PIDE_OK;
 }
@@ -117,6 +120,12 @@ pide_status make_tma_rhs(pide_ctx* c, int bn) {
                    128, bn);
 }
 
+pide_status make_tma_rhs_corr(pide_ctx* c, int bn) {
+  if (!c->Rc) return PIDE_EINVAL;
+  return encode_2d(&c->tmRc, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->Rc, c->n, c->ws_B,
+                   (uint64_t)c->ld, 128, bn);
+}
+
 // ---------------------------------------------------------------- workspace
 
 pide_status ensure_workspace(pide_ctx* c, int B) {
@@ -126,10 +135,14 @@ pide_status ensure_workspace(pide_ctx* c, int B) {
   if (c->col_scale) cudaFree(c->col_scale);
   if (c->colmax) cudaFree(c->colmax);
   if (c->Rf) cudaFree(c->Rf);
+  if (c->Rc) cudaFree(c->Rc);
+  if (c->col_scale_c) cudaFree(c->col_scale_c);
   c->R = nullptr;
   c->col_scale = nullptr;
   c->colmax = nullptr;
   c->Rf = nullptr;
+  c->Rc = nullptr;
+  c->col_scale_c = nullptr;
   c->ws_B = 0;
   const size_t esz = c->prec == PIDE_FP64 ? 8 : 4;
   PIDE_CUDA_TRY(cudaMalloc(&c->R, (size_t)nb * c->ld * esz));
@@ -137,6 +150,10 @@ pide_status ensure_workspace(pide_ctx* c, int B) {
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->col_scale, (size_t)nb * sizeof(float)));
   if (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2)
     PIDE_CUDA_TRY(cudaMalloc((void**)&c->Rf, (size_t)nb * c->ld * sizeof(float)));
+  if (c->corr) {
+    PIDE_CUDA_TRY(cudaMalloc(&c->Rc, (size_t)nb * c->ld));
+    PIDE_CUDA_TRY(cudaMalloc((void**)&c->col_scale_c, (size_t)nb * sizeof(float)));
+  }
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->colmax, 3 * (size_t)nb * sizeof(double)));
   PIDE_CUDA_TRY(cudaMemset(c->colmax, 0, 3 * (size_t)nb * sizeof(double)));
   c->ws_B = nb;
@@ -202,7 +219,10 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
   const int rf = rhs_format(c, B);
   const bool tensor = B > c->gemv_max_b && (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 ||
                                             c->prec == PIDE_FP8X2);
-  if (c->overlap && tensor && tol <= 0 && sweeps > 0 && B >= 512 && c->aux)
+  // the e4m3 correction term joins the applies that corr_mask selects (tensor path)
+  const bool corr = c->corr && tensor && c->prec == PIDE_BF16;
+  auto corr_at = [&](int k) { return corr && k < 31 && ((c->corr_mask >> k) & 1); };
+  if (c->overlap && tensor && tol <= 0 && sweeps > 0 && B >= 512 && c->aux && !corr)
     return solve_overlapped(c, b, mode, lift, x, B, sweeps, rf, st);
   // Low-precision stores take the double-float residual (its ~2^-45 |u|
   // rounding is far below their own error) unless the caller's tolerance
@@ -212,7 +232,9 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
                     (tol <= 0 || tol >= 1e-8);
   if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
   PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st, emul));
+  if (corr_at(0)) PIDE_TRY(launch_corr_rhs(c, B, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
+  if (corr_at(0)) PIDE_TRY(launch_apply_corr(c, B, x, st));
   for (int k = 0; k < sweeps; ++k) {
     if (rf == RF_E4M3 && tol <= 0) {
       PIDE_TRY(launch_residual_fp8(c, b, x, B, mode, lift, st, emul));
@@ -223,7 +245,9 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
     PIDE_TRY(launch_residual(c, b, x, B, mode, lift, rf, true, nullptr, tol > 0, true, st, 0,
                              emul));
     if (tol > 0) PIDE_TRY(launch_check(c, B, tol, st));
+    if (corr_at(k + 1)) PIDE_TRY(launch_corr_rhs(c, B, st));
     PIDE_TRY(launch_apply(c, B, x, true, st));
+    if (corr_at(k + 1)) PIDE_TRY(launch_apply_corr(c, B, x, st));
   }
   return PIDE_OK;
 }
@@ -372,6 +396,8 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
+  const bool want_corr = p == PIDE_BF16_FP8;   // the BF16 store plus its e4m3 correction term
+  if (want_corr) p = PIDE_BF16;
   c->prec = p;
   pide_status s = setup_operator(c, nx, ny, nz, h, dims, eps_host, st);
   double* G = nullptr;
@@ -394,6 +420,7 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
       G = nullptr;
     } else {
       s = quantize_store(c, G, st);
+      if (s == PIDE_OK && want_corr) s = quantize_corr(c, G, st);
       if (s == PIDE_OK && p == PIDE_BF16) s = build_sym_store(c, G, st);
     }
   }
@@ -419,7 +446,7 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
 extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
                                   void* stream, pide_handle* out) {
   if (out) *out = nullptr;
-  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 4) {
+  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 5) {
     set_error("pide_setup: bad argument");
     return PIDE_EINVAL;
   }
@@ -431,7 +458,7 @@ extern "C" pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host
   if (out) *out = nullptr;
   const bool ok = g && g->nx >= 3 && g->ny >= 3 && g->nz >= 3 && std::isfinite(g->h) && g->h > 0 &&
                   (int64_t)(g->nx - 2) * (g->ny - 2) * (g->nz - 2) < (int64_t)1 << 30;
-  if (!out || !ok || (int)p < 0 || (int)p > 4) {
+  if (!out || !ok || (int)p < 0 || (int)p > 5) {
     set_error("pide_setup_3d: bad argument");
     return PIDE_EINVAL;
   }
@@ -443,6 +470,7 @@ extern "C" void pide_destroy(pide_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {h->sym, h->sym_lo, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
+                  h->corr, h->corr_scale, h->Rc, h->col_scale_c,
                   h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -748,7 +776,7 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
   hd.version = h->dims == 3 ? 2 : 1;
   hd.nx = h->nx;
   hd.ny = h->ny;
-  hd.prec = (int)h->prec;
+  hd.prec = h->corr ? (int)PIDE_BF16_FP8 : (int)h->prec;
   hd.n = h->n;
   hd.ld = h->ld;
   hd.h = h->h;
@@ -771,6 +799,10 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
   dump(h->inv, main_bytes);
   if (h->inv_lo) dump(h->inv_lo, main_bytes);
   if (h->row_scale) dump(h->row_scale, (size_t)h->n * sizeof(float));
+  if (h->corr) {
+    dump(h->corr, (size_t)h->n * h->ld);
+    dump(h->corr_scale, (size_t)h->n * sizeof(float));
+  }
   ok = (std::fclose(f) == 0) && ok;
   if (!ok) {
     set_error(std::string("writing ") + path + " failed");
@@ -797,7 +829,7 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   FileHeader3 h3{1, 2};
   if (ok && hd.version == 2) ok = std::fread(&h3, sizeof(h3), 1, f) == 1 && h3.dims == 3;
   pide_grid g{hd.nx, hd.ny, hd.h};
-  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 4 || h3.nz < 1 ||
+  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 5 || h3.nz < 1 ||
       (h3.dims == 3 && (h3.nz < 3 || (int64_t)(hd.nx - 2) * (hd.ny - 2) * (h3.nz - 2) >= (int64_t)1 << 30))) {
     std::fclose(f);
     set_error(std::string(path) + ": not a pide inverse file");
@@ -812,7 +844,8 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   }
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
-  c->prec = (pide_precision)hd.prec;
+  const bool has_corr = hd.prec == PIDE_BF16_FP8;
+  c->prec = has_corr ? PIDE_BF16 : (pide_precision)hd.prec;
   pide_status s = setup_operator(c, g.nx, g.ny, h3.nz, g.h, h3.dims, eps.data(), st);
   if (s == PIDE_OK && (c->n != hd.n || c->ld != hd.ld)) {
     set_error("pide_load: header sizes do not match the grid");
@@ -842,9 +875,12 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   if (s == PIDE_OK && c->prec == PIDE_FP8X2) s = load(&c->inv_lo, hd.store_bytes);
   if (s == PIDE_OK && (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2))
     s = load((void**)&c->row_scale, (size_t)c->n * sizeof(float));
+  if (s == PIDE_OK && has_corr) s = load(&c->corr, (size_t)c->n * c->ld);
+  if (s == PIDE_OK && has_corr) s = load((void**)&c->corr_scale, (size_t)c->n * sizeof(float));
   std::fclose(f);
   if (s == PIDE_OK) {
-    c->store_bytes = hd.store_bytes * (c->prec == PIDE_FP8X2 ? 2 : 1);
+    c->store_bytes = hd.store_bytes * (c->prec == PIDE_FP8X2 ? 2 : 1) +
+                     (has_corr ? (size_t)c->n * c->ld + c->n * sizeof(float) : 0);
     s = make_tma_maps(c);
   }
   if (s == PIDE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PIDE_ECUDA;
@@ -867,7 +903,7 @@ extern "C" pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out
   }
   out->n = h->n;
   out->ld = h->ld;
-  out->precision = (int32_t)h->prec;
+  out->precision = h->corr ? (int32_t)PIDE_BF16_FP8 : (int32_t)h->prec;
   out->num_sms = h->num_sms;
   out->store_bytes = h->store_bytes;
   out->setup_ms = h->setup_ms;
@@ -964,6 +1000,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value < 0 || value > 4096) break;
       h->resid_prefetch = value;
       return PIDE_OK;
+    case PIDE_TUNE_CORR_MASK:
+      if (value < 0 || value >= (1 << 30)) break;
+      h->corr_mask = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -988,6 +1028,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_GEMM_2CTA: *value = h->gemm_2cta; return PIDE_OK;
     case PIDE_TUNE_GEMM_A_HINT: *value = h->gemm_a_hint; return PIDE_OK;
     case PIDE_TUNE_RESID_PREFETCH: *value = h->resid_prefetch; return PIDE_OK;
+    case PIDE_TUNE_CORR_MASK: *value = h->corr_mask; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

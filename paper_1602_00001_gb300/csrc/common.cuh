@@ -69,6 +69,10 @@ struct pide_ctx {
   void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / e4m3 (hi)
   void* inv_lo = nullptr;           // [n][ld] e4m3 lo term (FP8X2)
   float* row_scale = nullptr;       // [n] per-row scale (FP8 formats)
+  // PIDE_BF16_FP8: e4m3 correction term of the BF16 store (prec stays PIDE_BF16)
+  void* corr = nullptr;             // [n][ld] e4m3((L^-1 - bf16(L^-1)) / corr_scale)
+  float* corr_scale = nullptr;      // [n] its per-row scale
+  int corr_mask = 2;                // applies that add it: bit 0 the first, bit k sweep k
   size_t store_bytes = 0;
   void* sym = nullptr;              // packed lower 128x128 BF16 tiles of S^-1, hi term (B = 1 apply)
   void* sym_lo = nullptr;           // same layout, lo term bf16(S^-1 - hi)
@@ -78,11 +82,15 @@ struct pide_ctx {
   float* ysum = nullptr;            // [n] FP32 accumulation of the symmetric apply
   bool tmA_ok = false;
   CUtensorMap tmA, tmA_lo;          // TMA maps over the stored inverse (tensor-core formats)
+  CUtensorMap tmA_corr;             // over the correction term (PIDE_BF16_FP8)
   // workspace (grown on demand; pide_reserve pre-sizes it)
   int ws_B = 0;
   void* R = nullptr;                // [ws_B][ld] quantised right-hand side / residual
   float* col_scale = nullptr;       // [ws_B] per-column scale (FP8 formats)
   float* Rf = nullptr;              // [ws_B][ld] FP32 residual before FP8 quantisation
+  void* Rc = nullptr;               // [ws_B][ld] e4m3 copy of the BF16 R for the correction term
+  float* col_scale_c = nullptr;     // [ws_B] its per-column scale
+  CUtensorMap tmRc;
   double* lift = nullptr;           // [n] boundary lifting sum_q w_pq g_q
   double* colmax = nullptr;         // [3][ws_B] column maxima: |r|, |b|, raw (FP8 scales)
   uint32_t* flags = nullptr;        // FLAG_COUNT words
@@ -180,14 +188,19 @@ pide_status launch_colmax_b(pide_ctx* c, const double* b, int B, int mode, const
 // Apply: u (=|+=) Q(L^-1) R for B columns.
 pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
                          int col0 = 0);
+// PIDE_BF16_FP8: R (BF16) -> Rc = e4m3(R / t_j), t_j = max|R_j| / 448; then
+// u += s_p t_j (C Rc) on the tensor cores.
+pide_status launch_corr_rhs(pide_ctx* c, int B, cudaStream_t st);
+pide_status launch_apply_corr(pide_ctx* c, int B, double* u, cudaStream_t st);
+pide_status quantize_corr(pide_ctx* c, const double* G, cudaStream_t st);
 int rhs_format(const pide_ctx* c, int B);   // element format R must hold for this B
 
 // tensor-core GEMM (BF16, FP8X2) and SIMT paths
 pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                           int col0 = 0);
+                           int col0 = 0, bool corr = false);
 // the same on pairs of SMs (tcgen05 cta_group::2, 256 x 256 tiles), for B > 128
 pide_status launch_gemm_tc2(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                            int col0 = 0);
+                            int col0 = 0, bool corr = false);
 pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 pide_status build_sym_store(pide_ctx* c, const double* G, cudaStream_t st);   // G = L^-1 (FP64)
 pide_status launch_symv(pide_ctx* c, double* u, bool accumulate, cudaStream_t st);
@@ -203,6 +216,7 @@ pide_status make_tma_maps(pide_ctx* c);
 pide_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
                       uint64_t outer, uint64_t row_bytes, uint32_t box_in, uint32_t box_out);
 pide_status make_tma_rhs(pide_ctx* c, int bn);
+pide_status make_tma_rhs_corr(pide_ctx* c, int bn);   // tmRc over Rc (e4m3)
 
 // event profiling around one launch of class `cls`
 struct ProfScope {

@@ -285,6 +285,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tmem_ld_wait();
         const int colbase = nt * BN + ch * 32;
         if (prow) {
+          // the 32 old values first: loads issued together instead of one
+          // load-add-store round trip per column (the stores through u
+          // could alias later loads, so the compiler keeps them in order)
+          double old[32];
+          if (accumulate && whole) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              old[j] = (colbase + j < B) ? u[(size_t)(colbase + j) * n + p] : 0.0;
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = colbase + j;
@@ -296,7 +305,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
               if (!whole) atomicAdd(dst, val);
-              else *dst = accumulate ? *dst + val : val;
+              else *dst = accumulate ? old[j] + val : val;
             }
           }
         }
@@ -329,11 +338,12 @@ __global__ void zero_tiles_kernel(double* __restrict__ u, int n, int B, int bm, 
 }
 
 template <int BN, int STAGES, int MODE>
-pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st, int col0) {
+pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st, int col0,
+                      bool corr) {
   using C = TcCfg<BN, MODE != 0>;
   constexpr int A_STAGE = (MODE == 2) ? 2 * C::A_BYTES : C::A_BYTES;
   const size_t smem = 1024 + (size_t)STAGES * (A_STAGE + C::B_BYTES) + 256;
-  PIDE_TRY(make_tma_rhs(c, BN));
+  PIDE_TRY(corr ? make_tma_rhs_corr(c, BN) : make_tma_rhs(c, BN));
   auto kern = gemm_tc_kernel<BN, STAGES, MODE>;
   PIDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int m_tiles = (c->n + BM - 1) / BM;
@@ -355,32 +365,37 @@ pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream
                                                          c->flags);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
-  kern<<<grid, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, col0, num_kb, dp_tiles, sk,
-                                u, accumulate ? 1 : 0, c->row_scale,
-                                MODE != 0 ? c->col_scale + col0 : nullptr, c->flags, c->gemm_a_hint);
+  // the correction term: e4m3 C against Rc, scales s_p (rows) and t_j (columns)
+  const CUtensorMap& A = corr ? c->tmA_corr : c->tmA;
+  const CUtensorMap& Alo = corr ? c->tmA_corr : c->tmA_lo;
+  const CUtensorMap& R = corr ? c->tmRc : c->tmR;
+  const float* rs = corr ? c->corr_scale : c->row_scale;
+  const float* cs = corr ? c->col_scale_c + col0 : (MODE != 0 ? c->col_scale + col0 : nullptr);
+  kern<<<grid, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, sk, u,
+                                accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
 
 template <int MODE>
 pide_status launch_tc_mode(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                           int col0) {
+                           int col0, bool corr = false) {
   // BN: the smallest supported tile that covers B (up to 256); stages fill ~200 KB.
   if (MODE == 0) {
-    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0);
-    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0);
-    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0);
-    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0, corr);
+    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0, corr);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0, corr);
+    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st, col0, corr);
   } else if (MODE == 1) {
-    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0);
-    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0);
-    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0);
-    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0, corr);
+    if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0, corr);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0, corr);
+    return launch_tc<256, 4, MODE>(c, B, u, accumulate, st, col0, corr);
   } else {
-    if (B <= 32) return launch_tc<32, 6, MODE>(c, B, u, accumulate, st, col0);
-    if (B <= 64) return launch_tc<64, 5, MODE>(c, B, u, accumulate, st, col0);
-    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 4, MODE>(c, B, u, accumulate, st, col0);
-    return launch_tc<256, 3, MODE>(c, B, u, accumulate, st, col0);
+    if (B <= 32) return launch_tc<32, 6, MODE>(c, B, u, accumulate, st, col0, corr);
+    if (B <= 64) return launch_tc<64, 5, MODE>(c, B, u, accumulate, st, col0, corr);
+    if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 4, MODE>(c, B, u, accumulate, st, col0, corr);
+    return launch_tc<256, 3, MODE>(c, B, u, accumulate, st, col0, corr);
   }
 }
 
@@ -395,13 +410,14 @@ pide_status launch_zero_tiles(pide_ctx* c, double* u, int B, int bm, int bn, int
 }
 
 pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                           int col0) {
+                           int col0, bool corr) {
   if (c->gemm_2cta && B > 128 && c->gemm_bn_large == 256)
-    return launch_gemm_tc2(c, B, u, accumulate, st, col0);
+    return launch_gemm_tc2(c, B, u, accumulate, st, col0, corr);
   if (!c->tmA_ok) {
     set_error("tensor-core apply: TMA maps were not created");
     return PIDE_EUNSUPPORTED;
   }
+  if (corr) return launch_tc_mode<1>(c, B, u, true, st, col0, true);
   switch (c->prec) {
     case PIDE_BF16: return launch_tc_mode<0>(c, B, u, accumulate, st, col0);
     case PIDE_FP8: return launch_tc_mode<1>(c, B, u, accumulate, st, col0);

@@ -360,6 +360,14 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         tmem_ld_wait();
         const int colbase = nt * BN2 + ch * 32;
         if (prow) {
+          // the 32 old values first: loads issued together instead of one
+          // load-add-store round trip per column
+          double old[32];
+          if (accumulate && whole) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              old[j] = (colbase + j < B) ? u[(size_t)(colbase + j) * n + p] : 0.0;
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = colbase + j;
@@ -369,7 +377,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
               if (!whole) atomicAdd(dst, val);
-              else *dst = accumulate ? *dst + val : val;
+              else *dst = accumulate ? old[j] + val : val;
             }
           }
         }
@@ -401,11 +409,11 @@ pide_status launch_zero_tiles(pide_ctx* c, double* u, int B, int bm, int bn, int
 
 template <int STAGES, int MODE, int NACC>
 static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                              int col0) {
+                              int col0, bool corr) {
   constexpr int A_STAGE = (MODE == 2 ? 2 : 1) * HALF * ROW_BYTES2;
   constexpr int B_BYTES = HALF * ROW_BYTES2;
   const size_t smem = 1024 + (size_t)STAGES * (A_STAGE + B_BYTES) + 256;
-  PIDE_TRY(make_tma_rhs(c, HALF));
+  PIDE_TRY(corr ? make_tma_rhs_corr(c, HALF) : make_tma_rhs(c, HALF));
   auto kern = gemm_tc2_kernel<STAGES, MODE, NACC>;
   PIDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (c->max_pairs <= 0) {
@@ -438,24 +446,30 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const int sk = dp_tiles < tiles ? 1 : 0;
   if (sk && !accumulate)
     PIDE_TRY(launch_zero_tiles(c, u, B, BM2, BN2, n_tiles, dp_tiles, tiles - dp_tiles, st));
-  kern<<<2 * clusters, 192, smem, st>>>(c->tmA, c->tmA_lo, c->tmR, c->n, B, col0, num_kb, dp_tiles,
-                                        sk, u, accumulate ? 1 : 0, c->row_scale,
-                                        MODE != 0 ? c->col_scale + col0 : nullptr, c->flags, c->gemm_a_hint);
+  // the correction term: e4m3 C against Rc, scales s_p (rows) and t_j (columns)
+  const CUtensorMap& A = corr ? c->tmA_corr : c->tmA;
+  const CUtensorMap& Alo = corr ? c->tmA_corr : c->tmA_lo;
+  const CUtensorMap& R = corr ? c->tmRc : c->tmR;
+  const float* rs = corr ? c->corr_scale : c->row_scale;
+  const float* cs = corr ? c->col_scale_c + col0 : (MODE != 0 ? c->col_scale + col0 : nullptr);
+  kern<<<2 * clusters, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, sk, u,
+                                        accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
 
 // B > 128 on pairs of SMs (256 x 256 tiles); stages fill ~200 KB per SM.
 pide_status launch_gemm_tc2(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                            int col0) {
+                            int col0, bool corr) {
   if (!c->tmA_ok) {
     set_error("tensor-core apply: TMA maps were not created");
     return PIDE_EUNSUPPORTED;
   }
+  if (corr) return launch_tc2<6, 1, TC2_NACC>(c, B, u, true, st, col0, true);
   switch (c->prec) {
-    case PIDE_BF16: return launch_tc2<6, 0, TC2_NACC>(c, B, u, accumulate, st, col0);
-    case PIDE_FP8: return launch_tc2<6, 1, TC2_NACC>(c, B, u, accumulate, st, col0);
-    case PIDE_FP8X2: return launch_tc2<4, 2, TC2_NACC>(c, B, u, accumulate, st, col0);
+    case PIDE_BF16: return launch_tc2<6, 0, TC2_NACC>(c, B, u, accumulate, st, col0, false);
+    case PIDE_FP8: return launch_tc2<6, 1, TC2_NACC>(c, B, u, accumulate, st, col0, false);
+    case PIDE_FP8X2: return launch_tc2<4, 2, TC2_NACC>(c, B, u, accumulate, st, col0, false);
     default: return PIDE_EUNSUPPORTED;
   }
 }

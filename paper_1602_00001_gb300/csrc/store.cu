@@ -63,14 +63,20 @@ __global__ void to_fp8_kernel(const double* __restrict__ G, size_t ld, int n,
 
 __global__ void row_to_f64_kernel(const void* __restrict__ inv, const void* __restrict__ inv_lo,
                                   const float* __restrict__ row_scale, int fmt, size_t ld, int n,
-                                  int p, double* __restrict__ out) {
+                                  int p, double* __restrict__ out,
+                                  const __nv_fp8_e4m3* __restrict__ corr,
+                                  const float* __restrict__ corr_scale) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const size_t e = (size_t)p * ld + q;
     double v;
     switch (fmt) {
       case PIDE_FP64: v = reinterpret_cast<const double*>(inv)[e]; break;
       case PIDE_FP32: v = reinterpret_cast<const float*>(inv)[e]; break;
-      case PIDE_BF16: v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(inv)[e]); break;
+      case PIDE_BF16:
+        // with the e4m3 correction term: Q + s_p C, exact in FP64
+        v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(inv)[e]);
+        if (corr) v += (double)(float)corr[e] * (double)corr_scale[p];
+        break;
       default: {
         v = (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv)[e];
         if (inv_lo) v += (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv_lo)[e];
@@ -138,7 +144,7 @@ extern "C" pide_status pide_get_inverse_row(pide_handle h, int32_t p, double* ds
   double* tmp = nullptr;
   PIDE_CUDA_TRY(cudaMalloc(&tmp, h->n * sizeof(double)));
   row_to_f64_kernel<<<64, 256>>>(h->inv, h->inv_lo, h->row_scale, (int)h->prec, (size_t)h->ld,
-                                 h->n, p, tmp);
+                                 h->n, p, tmp, (const __nv_fp8_e4m3*)h->corr, h->corr_scale);
   cudaError_t e = cudaMemcpy(dst_host, tmp, h->n * sizeof(double), cudaMemcpyDeviceToHost);
   cudaFree(tmp);
   PIDE_CUDA_TRY(e);

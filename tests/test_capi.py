@@ -70,6 +70,26 @@ def test_oracle_binary_rounding_pins():
     assert O.round_bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
 
 
+def test_oracle_bf16_correction_pins():
+    """Q + s C against M: each entry within half an e4m3 step of |M - Q| (2^-4
+    relative) plus half the e4m3 subnormal quantum (2^-10 s); the correction
+    cuts the median error of Q alone by more than 8x; a row already exact in
+    BF16 has s = 1 and C = 0; C's entries stay inside the finite e4m3 range and
+    the largest reaches 448 on every nonzero row."""
+    rng = np.random.default_rng(2)
+    M = rng.standard_normal((40, 300)) * 10.0 ** rng.uniform(-6, 2, (40, 300))
+    M[7] = O.round_bf16(M[7])
+    Q, s, C = O.quantize_bf16_correction(M)
+    err_q = np.abs(M - Q)
+    err = np.abs(M - (Q + s[:, None] * C))
+    assert np.all(err <= 2.0 ** -4 * err_q + 2.0 ** -10 * s[:, None] * (1 + 1e-12))
+    assert np.median(err[err_q > 0] / err_q[err_q > 0]) < 1 / 8
+    assert s[7] == 1.0 and not np.any(C[7])
+    assert np.all(np.abs(C) <= 448)
+    rows = [p for p in range(40) if p != 7]
+    assert np.all(np.max(np.abs(C[rows]), axis=1) == 448)
+
+
 def test_oracle_e4m3_rounding_pins():
     """round_e4m3 against torch's float8_e4m3fn conversion of float32 values
     (normal and subnormal range, ties), inside the finite range."""
