@@ -295,7 +295,8 @@ class Solver:
                  "gemm_streamk": 4, "overlap": 5, "resid_ctas": 6, "symv": 7,
                  "resid_emul": 8, "resid_shape": 9,
                  "gemm_2cta": 10, "gemm_a_hint": 11,
-                 "resid_prefetch": 12, "corr_mask": 13}
+                 "resid_prefetch": 12, "corr_mask": 13,
+                 "gemm_u_hint": 14}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

@@ -1004,6 +1004,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value < 0 || value >= (1 << 30)) break;
       h->corr_mask = value;
       return PIDE_OK;
+    case PIDE_TUNE_GEMM_U_HINT:
+      if (value < 0 || value > 1) break;
+      h->gemm_u_hint = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -1029,6 +1033,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_GEMM_A_HINT: *value = h->gemm_a_hint; return PIDE_OK;
     case PIDE_TUNE_RESID_PREFETCH: *value = h->resid_prefetch; return PIDE_OK;
     case PIDE_TUNE_CORR_MASK: *value = h->corr_mask; return PIDE_OK;
+    case PIDE_TUNE_GEMM_U_HINT: *value = h->gemm_u_hint; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

@@ -105,6 +105,7 @@ struct pide_ctx {
   int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
   int gemm_2cta = 1;                // B > 128 on SM pairs (tcgen05 cta_group::2)
   int gemm_a_hint = 1;              // L2 policy of the inverse's TMA loads (policy_for_a)
+  int gemm_u_hint = 1;              // epilogue's u loads/stores: 0 plain, 1 L2 evict-first
   int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
   int overlap = 0;                  // residual of one column group under the GEMM of the other
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
@@ -324,6 +325,17 @@ __device__ __forceinline__ uint64_t policy_evict_normal() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
   return p;
+}
+
+// FP64 loads and stores with an L2 cache-policy hint (the GEMM epilogues' u)
+__device__ __forceinline__ double ld_f64_hint(const double* p, uint64_t policy) {
+  double v;
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(policy));
+  return v;
+}
+__device__ __forceinline__ void st_f64_hint(double* p, double v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
+               : "memory");
 }
 
 // L2 policy for the streamed inverse: 0 evict-first, 1 evict-normal, 2 evict-last

@@ -174,7 +174,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                 int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                 const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-                uint32_t* __restrict__ flags, int a_hint) {
+                uint32_t* __restrict__ flags, int a_hint, int u_hint) {
   constexpr bool FP8 = MODE != 0;
   constexpr bool LO = MODE == 2;
   constexpr int A_BYTES = HALF * ROW_BYTES2;                  // 16 KB
@@ -331,6 +331,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue (both CTAs)
     const int quarter = warp & 3;
+    const uint64_t upol = policy_evict_first();     // used when u_hint
     const int row_in_tile = quarter * 32 + lane;
     int acc = 0;
     uint32_t acc_ph = 0;
@@ -364,9 +365,15 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           // load-add-store round trip per column
           double old[32];
           if (accumulate && whole) {
+            if (u_hint) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              old[j] = (colbase + j < B) ? u[(size_t)(colbase + j) * n + p] : 0.0;
+              for (int j = 0; j < 32; ++j)
+                old[j] = (colbase + j < B) ? ld_f64_hint(u + (size_t)(colbase + j) * n + p, upol) : 0.0;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                old[j] = (colbase + j < B) ? u[(size_t)(colbase + j) * n + p] : 0.0;
+            }
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -377,6 +384,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
               if (!whole) atomicAdd(dst, val);
+              else if (u_hint) st_f64_hint(dst, accumulate ? old[j] + val : val, upol);
               else *dst = accumulate ? old[j] + val : val;
             }
           }
@@ -453,7 +461,8 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const float* rs = corr ? c->corr_scale : c->row_scale;
   const float* cs = corr ? c->col_scale_c + col0 : (MODE != 0 ? c->col_scale + col0 : nullptr);
   kern<<<2 * clusters, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, sk, u,
-                                        accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint);
+                                        accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint,
+                                c->gemm_u_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
