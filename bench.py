@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 NODES = 200                  # grid nodes per side (Eq. 2), 198^2 interior unknowns
 BATCH = 1024                 # right-hand sides per step
-PRECISION = "bf16_fp8"
+PRECISION = "fp16_fp8"
 METRIC = "RHS solves/s at 198^2 grid, B=1 and 1024, refined BF16/FP8 vs FP64 apply @1e-6"
 UNIT = "RHS solves/s"
 TARGET_ERR = 0.5e-6          # calibration target (the bar is 1e-6)
@@ -282,16 +282,16 @@ def adjoint_workload(args):
     N, B = 128, 32
     h = 1.0 / (N - 1)
     eps = W.eps_lognormal(N, N, seed=4)
-    prec = args.precision or "bf16_fp8"
+    prec = args.precision or "fp16_fp8"
     s = Solver(N, N, h, eps, prec)
     b = s.rhs_from_charge(torch.from_numpy(W.gaussian_blobs(N, N, h, seed=40, batch=B)).cuda())
     ut = s.apply(s.rhs_from_charge(torch.from_numpy(W.gaussian_blobs(N, N, h, seed=41, batch=B)).cuda()), sweeps=6)
-    sweeps = args.sweeps if args.sweeps >= 0 else (2 if prec == "bf16_fp8" else 5)
+    sweeps = args.sweeps if args.sweeps >= 0 else {"bf16_fp8": 2, "fp16_fp8": 1, "fp16": 2}.get(prec, 5)
     # bytes each solve streams: the BF16 inverse every apply, the e4m3 correction
     # term (with its row scales) in the applies the correction mask selects
     n, ld = s.n, s.info().ld
-    hi_bytes = 2 * n * ld if prec in ("bf16", "bf16_fp8") else s.info().store_bytes
-    mask = s.get_tuning()["corr_mask"] if prec == "bf16_fp8" else 0
+    hi_bytes = 2 * n * ld if prec in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") else s.info().store_bytes
+    mask = s.get_tuning()["corr_mask"] if prec.endswith("_fp8") else 0
     n_corr = sum((mask >> k) & 1 for k in range(sweeps + 1))
     solve_bytes = (1 + sweeps) * hi_bytes + n_corr * (n * ld + 4 * n)
 
@@ -351,7 +351,7 @@ def threed_workload(args):
     torch.cuda.empty_cache()
     # 3-D: BF16 alone reaches the target in two sweeps, as the correction term does
     # (34^3 nodes: 215k against 180k solves/s), so BF16 is the default there
-    prec = args.precision if args.precision in ("bf16", "bf16_fp8") else "bf16"
+    prec = args.precision if args.precision in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") else "bf16"
     s = Solver3D(N, N, N, h, eps, prec)
     s.reserve(B)
     u = torch.empty_like(b)
@@ -488,9 +488,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default=None, choices=["bf16", "bf16_fp8", "fp8x2", "fp32"],
-                    help="stored format (default: bf16_fp8 for the 2-D apply, bf16 in 3-D, where "
-                         "the correction term saves no sweep)")
+    ap.add_argument("--precision", default=None,
+                    choices=["bf16", "bf16_fp8", "fp16", "fp16_fp8", "fp8x2", "fp32"],
+                    help="stored format (default: fp16_fp8 for the 2-D apply and the adjoint, "
+                         "bf16 in 3-D)")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
@@ -637,7 +638,8 @@ def main():
             s.apply(b1, u1, sweeps=k1)
     b1_apply_launches, b1_apply_ms = prof1["apply"]
     hi = s.info()
-    b1_bytes = hi.store_bytes if not (args.precision in ("bf16", "bf16_fp8") and s.get_tuning()["symv"]) else \
+    sym_b1 = args.precision in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") and s.get_tuning()["symv"]
+    b1_bytes = hi.store_bytes if not sym_b1 else \
         2 * 2 * (((n + 127) // 128) * (((n + 127) // 128) + 1) // 2) * 128 * 128
     b1_gbs = b1_bytes * b1_apply_launches / (b1_apply_ms * 1e-3) / 1e9
 
@@ -718,7 +720,7 @@ def main():
     launches = sum(prof[c][0] for c in prof)
     # PIDE_BF16_FP8: the correction term's e4m3 GEMM (profile class "other") on the FP8 pipe
     corr_line = None
-    if args.precision == "bf16_fp8" and prof["other"][0] > 0:
+    if args.precision.endswith("_fp8") and prof["other"][0] > 0:
         c_launches, c_ms = prof["other"]
         c_tf = 2.0 * n * n * B * c_launches / (c_ms * 1e-3) / 1e12
         c_peak = pk["bf16_tflops_sustained"] * 2.0
@@ -737,13 +739,13 @@ def main():
                    "global_batch": B * world, "per_gpu_batch": B,
                    "grid": f"{NN}x{NN}", "unknowns": n, "precision": args.precision,
                    "sweeps": k, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (3.07 GB BF16 inverse streamed per apply, "
-                         "1.54 GB e4m3 correction term per correcting sweep)"},
+                   "l2": f"inputs larger than L2 ({hi.store_bytes / 1e9:.2f} GB stored inverse "
+                         f"({args.precision}) streamed per apply)"},
         "accuracy": {"max_rel_err_eq6_vs_fp64": err_final, "target": 1e-6,
                      "sampled_columns": len(sample_cols),
                      "err_by_sweeps": {str(kk): v for kk, v in calib.items()}},
         "b1": {"value": 1.0 / (b1_ms * 1e-3), "unit": UNIT, "sweeps": k1, "ms": b1_ms,
-               "path": "symmetric S^-1, BF16 hi+lo packed lower tiles" if (args.precision in ("bf16", "bf16_fp8") and s.get_tuning()["symv"]) else "GEMV over the stored L^-1",
+               "path": "symmetric S^-1, BF16 hi+lo packed lower tiles" if sym_b1 else "GEMV over the stored L^-1",
                "roofline": {"bound": "hbm", "achieved": b1_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                             "frac": b1_gbs / pk["hbm_gbs"], "bytes_per_apply": b1_bytes,
                             "avg_apply_ms": b1_apply_ms / max(b1_apply_launches, 1)}},

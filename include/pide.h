@@ -64,12 +64,21 @@ typedef enum {
   PIDE_BF16 = 2,   /* BF16 inverse, tensor-core apply (FP32 accumulate), FP64 refinement */
   PIDE_FP8 = 3,    /* e4m3 inverse with per-row scales (single term; study only) */
   PIDE_FP8X2 = 4,  /* e4m3 hi + lo terms with per-row scales, FP8 tensor cores */
-  PIDE_BF16_FP8 = 5 /* BF16 inverse Q plus an e4m3 correction term C with its own per-row
+  PIDE_BF16_FP8 = 5, /* BF16 inverse Q plus an e4m3 correction term C with its own per-row
                        scales s_p: C = e4m3((L^-1 - Q) / s_p).  Every apply contracts Q on the
                        BF16 tensor cores; the applies that PIDE_TUNE_CORR_MASK selects add
                        s_p t_j (C e4m3(R / t_j)) on the FP8 tensor cores (t_j = max|R_j| / 448),
                        which cuts that sweep's error by a further ~2^-4 (B = 2..65535 only:
                        B = 1 and the batched entry points use Q alone) */
+  PIDE_FP16 = 6,    /* FP16 inverse Q_p = fp16(L^-1_p / s_p) with power-of-two row scales s_p
+                       (row maximum in [2^14, 2^15)), FP16 right-hand sides with power-of-two
+                       column scales t_j set once per apply from the first right-hand side
+                       (column maximum in [2^11, 2^12)), tensor-core apply on the FP16 pipe
+                       (the BF16 rate) with u += s_p t_j acc: 11 significant bits where BF16
+                       has 8.  B = 1 uses the symmetric two-term BF16 store as PIDE_BF16 does;
+                       not served by the batched entry points */
+  PIDE_FP16_FP8 = 7 /* PIDE_FP16 plus the e4m3 correction term of PIDE_BF16_FP8, taken against
+                       the FP16 store; PIDE_TUNE_CORR_MASK defaults to 1 (the first apply) */
 } pide_precision;
 
 typedef struct {
@@ -356,10 +365,11 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           each block prefetches its tile of the pair that many pairs ahead
  *                           (0 = none, up to 4096; default 4: the 2-D residual at 158^2 and
  *                           198^2 unknowns, B = 1024, 12-15% faster, 3-D unchanged)
- *   PIDE_TUNE_CORR_MASK       PIDE_BF16_FP8 handles: bit k set = apply k adds the e4m3
- *                           correction term (bit 0: the first apply, bit k: refinement sweep k;
- *                           0 .. 2^30 - 1; default 2, the first sweep: at 198^2 unknowns,
- *                           B = 1024, two sweeps then reach ~2e-7 where BF16 alone needs four)
+ *   PIDE_TUNE_CORR_MASK       PIDE_BF16_FP8 / PIDE_FP16_FP8 handles: bit k set = apply k adds
+ *                           the e4m3 correction term (bit 0: the first apply, bit k: refinement
+ *                           sweep k; 0 .. 2^30 - 1; default 2 for PIDE_BF16_FP8, the first
+ *                           sweep: at 198^2 unknowns, B = 1024, two sweeps then reach ~2e-7 where
+ *                           BF16 alone needs four; default 1 for PIDE_FP16_FP8)
  *   PIDE_TUNE_GEMM_U_HINT     tensor-core GEMM epilogues: 1 (default) = load and store u with
  *                           an L2 evict-first hint (keeps the streamed inverse's lines in L2:
  *                           at 198^2, B = 1024, DRAM reads per accumulating launch 6.5 -> 5.2 GB,

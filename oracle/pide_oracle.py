@@ -521,6 +521,50 @@ def quantize_rows_e4m3(M: np.ndarray, two_terms: bool):
     return s, hi, lo
 
 
+def round_fp16(x: np.ndarray) -> np.ndarray:
+    """IEEE binary16 value of each entry, nearest with ties to even: 11
+    significant bits for |x| >= 2^-14, the fixed quantum 2^-24 below
+    (subnormals); saturating at the largest finite value 65504."""
+    x = np.asarray(x, dtype=np.float64)
+    normal = round_to_bits(x, 11)
+    sub = np.rint(x / 2.0 ** -24) * 2.0 ** -24
+    out = np.where(np.abs(x) >= 2.0 ** -14, normal, sub)
+    return np.clip(out, -65504.0, 65504.0)
+
+
+def pow2_scale(mx: np.ndarray, top: int) -> np.ndarray:
+    """2^k with mx / 2^k in [2^(top-1), 2^top) (1 where mx = 0); k kept in
+    float32's normal exponent range [-126, 127]."""
+    mx = np.asarray(mx, dtype=np.float64)
+    _, e = np.frexp(mx)                       # mx = m 2^e, 0.5 <= m < 1
+    k = np.clip(e - top, -126, 127)
+    return np.where(mx > 0, np.ldexp(1.0, k), 1.0)
+
+
+def quantize_rows_fp16(M: np.ndarray):
+    """Per-row FP16 storage with power-of-two scales: s_p = 2^k with
+    max_q |M_pq| / s_p in [2^14, 2^15); Q = fp16(M / s) (the scaling exact, one
+    rounding).  Returns (s, Q) with M ~ s Q."""
+    s = pow2_scale(np.max(np.abs(M), axis=1), 15)
+    return s, round_fp16(M / s[:, None])
+
+
+def quantize_cols_fp16(F: np.ndarray):
+    """FP16 right-hand sides [B][n] with power-of-two column scales: t_j = 2^k
+    with max_p |F_jp| / t_j in [2^11, 2^12); R = fp16(F / t).  Returns (t, R)."""
+    t = pow2_scale(np.max(np.abs(F), axis=1), 12)
+    return t, round_fp16(F / t[:, None])
+
+
+def quantize_fp16_correction(M: np.ndarray):
+    """The FP16 store with an e4m3 correction term: (s, Q) = quantize_rows_fp16(M);
+    D = M - s Q (exact); (c, C) the per-row e4m3 quantisation of D as in
+    quantize_rows_e4m3.  Returns (s, Q, c, C) with M ~ s Q + c C."""
+    s, Q = quantize_rows_fp16(M)
+    c, C, _ = quantize_rows_e4m3(M - s[:, None] * Q, False)
+    return s, Q, c, C
+
+
 def quantize_bf16_correction(M: np.ndarray):
     """The BF16 store with an e4m3 correction term, written out: Q = bf16(M);
     D = M - Q (exact in FP64: Q holds the leading bits of M); per-row scale

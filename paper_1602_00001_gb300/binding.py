@@ -15,7 +15,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpide.so")
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8x2": 4, "bf16_fp8": 5}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8x2": 4, "bf16_fp8": 5, "fp16": 6,
+              "fp16_fp8": 7}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
           6: "EUNSUPPORTED"}
 
@@ -135,9 +136,10 @@ class Solver:
     """One operator (grid + node permittivity) with its stored inverse.
 
     ``precision``: 'fp64' (plain FP64 inverse and apply), 'fp32', 'bf16',
-    'fp8' or 'fp8x2' (low-precision inverse, FP64 refinement), or 'bf16_fp8'
-    (BF16 inverse plus an e4m3 correction term added in the sweeps that the
-    'corr_mask' tuning key selects).
+    'fp8' or 'fp8x2' (low-precision inverse, FP64 refinement), 'fp16' (FP16
+    inverse and right-hand sides with power-of-two row / column scales), or
+    'bf16_fp8' / 'fp16_fp8' (the BF16 / FP16 inverse plus an e4m3 correction
+    term added in the applies that the 'corr_mask' tuning key selects).
     """
 
     def __init__(self, nx: int, ny: int, h: float, eps=None, precision: str = "bf16",

@@ -32,6 +32,7 @@ int rhs_format(const pide_ctx* c, int B) {
     case PIDE_FP64: return RF_F64;
     case PIDE_FP32: return RF_F32;
     case PIDE_BF16: return B <= c->gemv_max_b ? RF_F32 : RF_BF16;
+    case PIDE_FP16: return B <= c->gemv_max_b ? RF_F32 : RF_F16;
     default: return B <= c->gemv_max_b ? RF_F32 : RF_E4M3;
   }
 }
@@ -91,9 +92,10 @@ pide_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base
 
 pide_status make_tma_maps(pide_ctx* c) {
   c->tmA_ok = false;
-  if (c->prec == PIDE_BF16) {
-    PIDE_TRY(encode_2d(&c->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c->inv, c->n, c->n,
-                       (uint64_t)c->ld * 2, 64, 128));
+  if (c->prec == PIDE_BF16 || c->prec == PIDE_FP16) {
+    PIDE_TRY(encode_2d(&c->tmA, c->prec == PIDE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                       c->inv, c->n, c->n, (uint64_t)c->ld * 2, 64, 128));
   } else if (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2) {
     PIDE_TRY(encode_2d(&c->tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->inv, c->n, c->n,
                        (uint64_t)c->ld, 128, 128));
@@ -113,9 +115,10 @@ pide_status make_tma_maps(pide_ctx* c) {
 }
 
 pide_status make_tma_rhs(pide_ctx* c, int bn) {
-  if (c->prec == PIDE_BF16)
-    return encode_2d(&c->tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c->R, c->n, c->ws_B,
-                     (uint64_t)c->ld * 2, 64, bn);
+  if (c->prec == PIDE_BF16 || c->prec == PIDE_FP16)
+    return encode_2d(&c->tmR, c->prec == PIDE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                     c->R, c->n, c->ws_B, (uint64_t)c->ld * 2, 64, bn);
   return encode_2d(&c->tmR, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->R, c->n, c->ws_B, (uint64_t)c->ld,
                    128, bn);
 }
@@ -218,20 +221,23 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
   PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, 3 * (size_t)c->ws_B * sizeof(double), st));
   const int rf = rhs_format(c, B);
   const bool tensor = B > c->gemv_max_b && (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 ||
-                                            c->prec == PIDE_FP8X2);
+                                            c->prec == PIDE_FP8X2 || c->prec == PIDE_FP16);
   // the e4m3 correction term joins the applies that corr_mask selects (tensor path)
-  const bool corr = c->corr && tensor && c->prec == PIDE_BF16;
+  const bool corr = c->corr && tensor && (c->prec == PIDE_BF16 || c->prec == PIDE_FP16);
   auto corr_at = [&](int k) { return corr && k < 31 && ((c->corr_mask >> k) & 1); };
-  if (c->overlap && tensor && tol <= 0 && sweeps > 0 && B >= 512 && c->aux && !corr)
+  if (c->overlap && tensor && tol <= 0 && sweeps > 0 && B >= 512 && c->aux && !corr &&
+      rf != RF_F16)
     return solve_overlapped(c, b, mode, lift, x, B, sweeps, rf, st);
   // Low-precision stores take the double-float residual (its ~2^-45 |u|
   // rounding is far below their own error) unless the caller's tolerance
   // asks for a residual below 1e-8 of |f|, which only the FP64 stencil resolves.
   const bool emul = c->resid_emul && mode == 0 &&
-                    (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2) &&
+                    (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2 ||
+                     c->prec == PIDE_FP16) &&
                     (tol <= 0 || tol >= 1e-8);
   if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
-  PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st, emul));
+  if (rf == RF_F16) PIDE_TRY(launch_prep_f16(c, b, B, mode, lift, tol > 0, st));
+  else PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st, emul));
   if (corr_at(0)) PIDE_TRY(launch_corr_rhs(c, B, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
   if (corr_at(0)) PIDE_TRY(launch_apply_corr(c, B, x, st));
@@ -396,8 +402,13 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
-  const bool want_corr = p == PIDE_BF16_FP8;   // the BF16 store plus its e4m3 correction term
-  if (want_corr) p = PIDE_BF16;
+  // the BF16 / FP16 store plus its e4m3 correction term
+  const bool want_corr = p == PIDE_BF16_FP8 || p == PIDE_FP16_FP8;
+  if (p == PIDE_BF16_FP8) p = PIDE_BF16;
+  if (p == PIDE_FP16_FP8) {
+    p = PIDE_FP16;
+    c->corr_mask = 1;                             // FP16: correct the first apply
+  }
   c->prec = p;
   pide_status s = setup_operator(c, nx, ny, nz, h, dims, eps_host, st);
   double* G = nullptr;
@@ -421,7 +432,8 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
     } else {
       s = quantize_store(c, G, st);
       if (s == PIDE_OK && want_corr) s = quantize_corr(c, G, st);
-      if (s == PIDE_OK && p == PIDE_BF16) s = build_sym_store(c, G, st);
+      // B = 1 of both 16-bit stores: the symmetric two-term BF16 form of S^-1
+      if (s == PIDE_OK && (p == PIDE_BF16 || p == PIDE_FP16)) s = build_sym_store(c, G, st);
     }
   }
   if (s == PIDE_OK) s = make_tma_maps(c);
@@ -446,7 +458,7 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
 extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
                                   void* stream, pide_handle* out) {
   if (out) *out = nullptr;
-  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 5) {
+  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 7) {
     set_error("pide_setup: bad argument");
     return PIDE_EINVAL;
   }
@@ -458,7 +470,7 @@ extern "C" pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host
   if (out) *out = nullptr;
   const bool ok = g && g->nx >= 3 && g->ny >= 3 && g->nz >= 3 && std::isfinite(g->h) && g->h > 0 &&
                   (int64_t)(g->nx - 2) * (g->ny - 2) * (g->nz - 2) < (int64_t)1 << 30;
-  if (!out || !ok || (int)p < 0 || (int)p > 5) {
+  if (!out || !ok || (int)p < 0 || (int)p > 7) {
     set_error("pide_setup_3d: bad argument");
     return PIDE_EINVAL;
   }
@@ -770,13 +782,14 @@ extern "C" pide_status pide_save(pide_handle h, const char* path) {
     return PIDE_EINVAL;
   }
   const size_t main_bytes = (size_t)h->n * h->ld *
-                            (h->prec == PIDE_FP64 ? 8 : h->prec == PIDE_FP32 ? 4 : h->prec == PIDE_BF16 ? 2 : 1);
+                            (h->prec == PIDE_FP64 ? 8 : h->prec == PIDE_FP32 ? 4 :
+                             (h->prec == PIDE_BF16 || h->prec == PIDE_FP16) ? 2 : 1);
   FileHeader hd{};
   std::memcpy(hd.magic, "PIDEINV1", 8);
   hd.version = h->dims == 3 ? 2 : 1;
   hd.nx = h->nx;
   hd.ny = h->ny;
-  hd.prec = h->corr ? (int)PIDE_BF16_FP8 : (int)h->prec;
+  hd.prec = !h->corr ? (int)h->prec : h->prec == PIDE_FP16 ? (int)PIDE_FP16_FP8 : (int)PIDE_BF16_FP8;
   hd.n = h->n;
   hd.ld = h->ld;
   hd.h = h->h;
@@ -829,7 +842,7 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   FileHeader3 h3{1, 2};
   if (ok && hd.version == 2) ok = std::fread(&h3, sizeof(h3), 1, f) == 1 && h3.dims == 3;
   pide_grid g{hd.nx, hd.ny, hd.h};
-  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 5 || h3.nz < 1 ||
+  if (!ok || !valid_grid(&g) || hd.prec < 0 || hd.prec > 7 || h3.nz < 1 ||
       (h3.dims == 3 && (h3.nz < 3 || (int64_t)(hd.nx - 2) * (hd.ny - 2) * (h3.nz - 2) >= (int64_t)1 << 30))) {
     std::fclose(f);
     set_error(std::string(path) + ": not a pide inverse file");
@@ -844,8 +857,10 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   }
   cudaStream_t st = (cudaStream_t)stream;
   pide_ctx* c = new pide_ctx();
-  const bool has_corr = hd.prec == PIDE_BF16_FP8;
-  c->prec = has_corr ? PIDE_BF16 : (pide_precision)hd.prec;
+  const bool has_corr = hd.prec == PIDE_BF16_FP8 || hd.prec == PIDE_FP16_FP8;
+  c->prec = hd.prec == PIDE_BF16_FP8 ? PIDE_BF16 : hd.prec == PIDE_FP16_FP8 ? PIDE_FP16
+                                                 : (pide_precision)hd.prec;
+  if (hd.prec == PIDE_FP16_FP8) c->corr_mask = 1;
   pide_status s = setup_operator(c, g.nx, g.ny, h3.nz, g.h, h3.dims, eps.data(), st);
   if (s == PIDE_OK && (c->n != hd.n || c->ld != hd.ld)) {
     set_error("pide_load: header sizes do not match the grid");
@@ -873,13 +888,14 @@ extern "C" pide_status pide_load(const char* path, void* stream, pide_handle* ou
   };
   if (s == PIDE_OK) s = load(&c->inv, hd.store_bytes);
   if (s == PIDE_OK && c->prec == PIDE_FP8X2) s = load(&c->inv_lo, hd.store_bytes);
-  if (s == PIDE_OK && (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2))
+  if (s == PIDE_OK && (c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2 || c->prec == PIDE_FP16))
     s = load((void**)&c->row_scale, (size_t)c->n * sizeof(float));
   if (s == PIDE_OK && has_corr) s = load(&c->corr, (size_t)c->n * c->ld);
   if (s == PIDE_OK && has_corr) s = load((void**)&c->corr_scale, (size_t)c->n * sizeof(float));
   std::fclose(f);
   if (s == PIDE_OK) {
     c->store_bytes = hd.store_bytes * (c->prec == PIDE_FP8X2 ? 2 : 1) +
+                     (c->prec == PIDE_FP16 ? c->n * sizeof(float) : 0) +
                      (has_corr ? (size_t)c->n * c->ld + c->n * sizeof(float) : 0);
     s = make_tma_maps(c);
   }
@@ -903,7 +919,8 @@ extern "C" pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out
   }
   out->n = h->n;
   out->ld = h->ld;
-  out->precision = h->corr ? (int32_t)PIDE_BF16_FP8 : (int32_t)h->prec;
+  out->precision = !h->corr ? (int32_t)h->prec
+                  : h->prec == PIDE_FP16 ? (int32_t)PIDE_FP16_FP8 : (int32_t)PIDE_BF16_FP8;
   out->num_sms = h->num_sms;
   out->store_bytes = h->store_bytes;
   out->setup_ms = h->setup_ms;

@@ -20,6 +20,7 @@ template <> struct Elem<KIND_F32> { using TA = float; using TX = float; static c
 template <> struct Elem<KIND_BF16> { using TA = __nv_bfloat16; using TX = float; static constexpr int VEC = 8; };
 template <> struct Elem<KIND_FP8> { using TA = __nv_fp8_e4m3; using TX = float; static constexpr int VEC = 16; };
 template <> struct Elem<KIND_FP8X2> { using TA = __nv_fp8_e4m3; using TX = float; static constexpr int VEC = 16; };
+template <> struct Elem<KIND_F16> { using TA = __half; using TX = float; static constexpr int VEC = 8; };
 
 template <int KIND>
 __device__ __forceinline__ void unpack(const uint4& raw, float (&out)[Elem<KIND>::VEC]) {
@@ -32,6 +33,14 @@ __device__ __forceinline__ void unpack(const uint4& raw, float (&out)[Elem<KIND>
     for (int i = 0; i < 4; ++i) {
       out[2 * i] = __uint_as_float(w[i] << 16);
       out[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  } else if constexpr (KIND == KIND_F16) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+      out[2 * i] = f.x;
+      out[2 * i + 1] = f.y;
     }
   } else {
     const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
@@ -259,6 +268,7 @@ pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStre
     case PIDE_BF16: return gemv_dispatch<KIND_BF16>(c, B, u, accumulate, st);
     case PIDE_FP8: return gemv_dispatch<KIND_FP8>(c, B, u, accumulate, st);
     case PIDE_FP8X2: return gemv_dispatch<KIND_FP8X2>(c, B, u, accumulate, st);
+    case PIDE_FP16: return gemv_dispatch<KIND_F16>(c, B, u, accumulate, st);   // row scales applied
   }
   return PIDE_EINVAL;
 }

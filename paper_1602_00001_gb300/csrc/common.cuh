@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
 
@@ -43,7 +44,7 @@ enum { FLAG_DONE = 0, FLAG_ERROR = 1, FLAG_SWEEPS = 2, FLAG_WHERE = 3, FLAG_COUN
 
 // ---------------------------------------------------------------- context
 
-enum ApplyKind { KIND_F64 = 0, KIND_F32 = 1, KIND_BF16 = 2, KIND_FP8 = 3, KIND_FP8X2 = 4 };
+enum ApplyKind { KIND_F64 = 0, KIND_F32 = 1, KIND_BF16 = 2, KIND_FP8 = 3, KIND_FP8X2 = 4, KIND_F16 = 6 };
 
 struct pide_ctx_impl;
 
@@ -66,10 +67,11 @@ struct pide_ctx {
                                     // (W,E,S,N) hi, (W,E,S,N) lo (, (D hi, U hi, D lo, U lo))
   std::vector<double> eps_host;     // kept for save/load
   // stored inverse L^-1 = S^-1 D (the interior block of the Fig. 3 inverse)
-  void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / e4m3 (hi)
+  void* inv = nullptr;              // [n][ld] FP64 / FP32 / BF16 / FP16 / e4m3 (hi)
   void* inv_lo = nullptr;           // [n][ld] e4m3 lo term (FP8X2)
-  float* row_scale = nullptr;       // [n] per-row scale (FP8 formats)
-  // PIDE_BF16_FP8: e4m3 correction term of the BF16 store (prec stays PIDE_BF16)
+  float* row_scale = nullptr;       // [n] per-row scale (FP8 formats; FP16: powers of two)
+  // PIDE_BF16_FP8 / PIDE_FP16_FP8: e4m3 correction term of the BF16 or FP16 store
+  // (prec stays PIDE_BF16 / PIDE_FP16)
   void* corr = nullptr;             // [n][ld] e4m3((L^-1 - bf16(L^-1)) / corr_scale)
   float* corr_scale = nullptr;      // [n] its per-row scale
   int corr_mask = 2;                // applies that add it: bit 0 the first, bit k sweep k
@@ -86,7 +88,7 @@ struct pide_ctx {
   // workspace (grown on demand; pide_reserve pre-sizes it)
   int ws_B = 0;
   void* R = nullptr;                // [ws_B][ld] quantised right-hand side / residual
-  float* col_scale = nullptr;       // [ws_B] per-column scale (FP8 formats)
+  float* col_scale = nullptr;       // [ws_B] per-column scale (FP8 formats; FP16: powers of two)
   float* Rf = nullptr;              // [ws_B][ld] FP32 residual before FP8 quantisation
   void* Rc = nullptr;               // [ws_B][ld] e4m3 copy of the BF16 R for the correction term
   float* col_scale_c = nullptr;     // [ws_B] its per-column scale
@@ -174,6 +176,12 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
                                const uint32_t* flags, cudaStream_t st);
 pide_status launch_prep_df_bf16(pide_ctx* c, const double* b, int B, const double* lift,
                                 bool track, cudaStream_t st);
+// FP16 right-hand sides (f16.cu): per column t_j = 2^k with max|f_j| / t_j in
+// [2^11, 2^12) into col_scale, R = fp16(f / t_j) rounded to nearest from FP64;
+// the refinement's residuals reuse t_j.
+pide_status launch_prep_f16(pide_ctx* c, const double* b, int B, int mode, const double* lift,
+                            bool track, cudaStream_t st);
+pide_status quantize_store_f16(pide_ctx* c, const double* G, cudaStream_t st);
 // Residual with a small persistent grid (num_sms * resid_ctas_per_sm blocks), for the
 // overlapped schedule; writes R only.
 pide_status launch_residual_persistent(pide_ctx* c, const double* b, const double* u, int B,
@@ -226,7 +234,7 @@ struct ProfScope {
   ~ProfScope();
 };
 
-enum RhsFmt { RF_F64 = 0, RF_F32 = 1, RF_BF16 = 2, RF_E4M3 = 3 };
+enum RhsFmt { RF_F64 = 0, RF_F32 = 1, RF_BF16 = 2, RF_E4M3 = 3, RF_F16 = 4 };
 
 size_t rhs_elem_bytes(int rfmt);
 

@@ -98,14 +98,15 @@ struct SegIter {
   }
 };
 
-template <int BN, int STAGES, int MODE>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo)
+template <int BN, int STAGES, int MODE>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo), 3: FP16 (row/column scales)
 __global__ void __launch_bounds__(192, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
                const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                const float* __restrict__ row_scale, const float* __restrict__ col_scale,
                uint32_t* __restrict__ flags, int a_hint, int u_hint) {
-  constexpr bool FP8 = MODE != 0;
+  constexpr bool FP8 = MODE == 1 || MODE == 2;   // kind::f8f6f4 (else kind::f16)
+  constexpr bool SCALED = MODE != 0;              // epilogue applies row and column scales
   constexpr bool LO = MODE == 2;
   using C = TcCfg<BN, FP8>;
   constexpr int A_STAGE = LO ? 2 * C::A_BYTES : C::A_BYTES;
@@ -196,8 +197,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     uint32_t idesc = (1u << 4)                                  // D: F32
-                     | ((FP8 ? 0u : 1u) << 7)                   // A: BF16 (kind::f16) / E4M3 (kind::f8f6f4)
-                     | ((FP8 ? 0u : 1u) << 10)                  // B: same
+                     | ((MODE == 0 ? 1u : 0u) << 7)             // A: BF16 / F16 (kind::f16), E4M3 (kind::f8f6f4)
+                     | ((MODE == 0 ? 1u : 0u) << 10)            // B: same
                      | ((uint32_t)(BN >> 3) << 17)              // N
                      | ((uint32_t)(BM >> 4) << 24);             // M
     int s = 0;
@@ -277,7 +278,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       tc_fence_after();
       const int p = mt * BM + row_in_tile;
       const bool prow = p < n;
-      const float rs = (FP8 && prow) ? row_scale[p] : 1.0f;
+      const float rs = (SCALED && prow) ? row_scale[p] : 1.0f;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ++ch) {
@@ -305,10 +306,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           for (int j = 0; j < 32; ++j) {
             const int col = colbase + j;
             if (col < B) {
-              // scales applied in FP32 (the FP8 apply is good to ~2^-8 anyway);
+              // scales applied in FP32 (powers of two for FP16: exact; the FP8
+              // apply is good to ~2^-8 anyway);
               // one FP64 operation per element: the add into u
               float a = __uint_as_float(v[j]);
-              if (FP8) a = a * rs * col_scale[col];
+              if (SCALED) a = a * rs * col_scale[col];
               const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
               if (!whole) atomicAdd(dst, val);
@@ -348,7 +350,7 @@ __global__ void zero_tiles_kernel(double* __restrict__ u, int n, int B, int bm, 
 template <int BN, int STAGES, int MODE>
 pide_status launch_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st, int col0,
                       bool corr) {
-  using C = TcCfg<BN, MODE != 0>;
+  using C = TcCfg<BN, MODE == 1 || MODE == 2>;
   constexpr int A_STAGE = (MODE == 2) ? 2 * C::A_BYTES : C::A_BYTES;
   const size_t smem = 1024 + (size_t)STAGES * (A_STAGE + C::B_BYTES) + 256;
   PIDE_TRY(corr ? make_tma_rhs_corr(c, BN) : make_tma_rhs(c, BN));
@@ -390,7 +392,7 @@ template <int MODE>
 pide_status launch_tc_mode(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
                            int col0, bool corr = false) {
   // BN: the smallest supported tile that covers B (up to 256); stages fill ~200 KB.
-  if (MODE == 0) {
+  if (MODE == 0 || MODE == 3) {
     if (B <= 32) return launch_tc<32, 10, MODE>(c, B, u, accumulate, st, col0, corr);
     if (B <= 64) return launch_tc<64, 8, MODE>(c, B, u, accumulate, st, col0, corr);
     if (B <= 128 || c->gemm_bn_large == 128) return launch_tc<128, 6, MODE>(c, B, u, accumulate, st, col0, corr);
@@ -431,6 +433,7 @@ pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaS
     case PIDE_BF16: return launch_tc_mode<0>(c, B, u, accumulate, st, col0);
     case PIDE_FP8: return launch_tc_mode<1>(c, B, u, accumulate, st, col0);
     case PIDE_FP8X2: return launch_tc_mode<2>(c, B, u, accumulate, st, col0);
+    case PIDE_FP16: return launch_tc_mode<3>(c, B, u, accumulate, st, col0);
     default: return PIDE_EUNSUPPORTED;
   }
 }

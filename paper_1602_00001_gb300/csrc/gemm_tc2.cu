@@ -168,14 +168,15 @@ struct SegIter2 {
 
 // NACC accumulators of 256 columns in tensor memory (2: the epilogue of one
 // tile overlaps the main loop of the next).
-template <int STAGES, int MODE, int NACC>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo)
+template <int STAGES, int MODE, int NACC>   // MODE 0: BF16, 1: FP8 (hi only), 2: FP8X2 (hi + lo), 3: FP16 (row/column scales)
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
                 const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                 int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                 const float* __restrict__ row_scale, const float* __restrict__ col_scale,
                 uint32_t* __restrict__ flags, int a_hint, int u_hint) {
-  constexpr bool FP8 = MODE != 0;
+  constexpr bool FP8 = MODE == 1 || MODE == 2;   // kind::f8f6f4 (else kind::f16)
+  constexpr bool SCALED = MODE != 0;              // epilogue applies row and column scales
   constexpr bool LO = MODE == 2;
   constexpr int A_BYTES = HALF * ROW_BYTES2;                  // 16 KB
   constexpr int A_STAGE = LO ? 2 * A_BYTES : A_BYTES;
@@ -270,8 +271,8 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else if (warp == 1 && lane == 0 && leader) {
     // ------------------------------------------------------------ MMA issuer (CTA 0)
     const uint32_t idesc = (1u << 4)                            // D: F32
-                           | ((FP8 ? 0u : 1u) << 7)             // A: BF16 / E4M3
-                           | ((FP8 ? 0u : 1u) << 10)            // B: same
+                           | ((MODE == 0 ? 1u : 0u) << 7)             // A: BF16 / F16 / E4M3
+                           | ((MODE == 0 ? 1u : 0u) << 10)            // B: same
                            | ((uint32_t)(BN2 >> 3) << 17)       // N = 256
                            | ((uint32_t)(BM2 >> 4) << 24);      // M = 256 (two SMs)
     int s = 0;
@@ -352,7 +353,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       tc_fence_after();
       const int p = mt * BM2 + (int)rank * HALF + row_in_tile;
       const bool prow = p < n;
-      const float rs = (FP8 && prow) ? row_scale[p] : 1.0f;
+      const float rs = (SCALED && prow) ? row_scale[p] : 1.0f;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN2);
 #pragma unroll 1
       for (int ch = 0; ch < BN2 / 32; ++ch) {
@@ -380,7 +381,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const int col = colbase + j;
             if (col < B) {
               float a = __uint_as_float(v[j]);
-              if (FP8) a = a * rs * col_scale[col];
+              if (SCALED) a = a * rs * col_scale[col];
               const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
               if (!whole) atomicAdd(dst, val);
@@ -437,7 +438,8 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const int m_tiles = (c->n + BM2 - 1) / BM2;
   const int n_tiles = (B + BN2 - 1) / BN2;
   const int tiles = m_tiles * n_tiles;
-  const int num_kb = (c->n + (MODE ? 128 : 64) - 1) / (MODE ? 128 : 64);
+  constexpr int KE = (MODE == 1 || MODE == 2) ? 128 : 64;   // K elements per stage
+  const int num_kb = (c->n + KE - 1) / KE;
   // The stream-K tail pays only when the data-parallel waves are few: at 198^2,
   // B = 1024 (8.1 waves) it measured the same time as whole tiles but 1.3-1.5 GB
   // more DRAM reads per launch; at B = 256 (2.0 waves) whole tiles would idle
@@ -479,6 +481,7 @@ pide_status launch_gemm_tc2(pide_ctx* c, int B, double* u, bool accumulate, cuda
     case PIDE_BF16: return launch_tc2<6, 0, TC2_NACC>(c, B, u, accumulate, st, col0, false);
     case PIDE_FP8: return launch_tc2<6, 1, TC2_NACC>(c, B, u, accumulate, st, col0, false);
     case PIDE_FP8X2: return launch_tc2<4, 2, TC2_NACC>(c, B, u, accumulate, st, col0, false);
+    case PIDE_FP16: return launch_tc2<6, 3, TC2_NACC>(c, B, u, accumulate, st, col0, false);
     default: return PIDE_EUNSUPPORTED;
   }
 }

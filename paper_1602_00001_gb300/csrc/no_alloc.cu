@@ -90,6 +90,7 @@ __device__ __forceinline__ float stored_entry(const void* inv, const void* inv_l
     case PIDE_FP64: return (float)reinterpret_cast<const double*>(inv)[e];
     case PIDE_FP32: return reinterpret_cast<const float*>(inv)[e];
     case PIDE_BF16: return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(inv)[e]);
+    case PIDE_FP16: return __half2float(reinterpret_cast<const __half*>(inv)[e]);   // row scale outside
     default: {
       float v = (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv)[e];
       if (inv_lo) v += (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv_lo)[e];

@@ -128,6 +128,10 @@ __device__ __forceinline__ void store_rhs(void* R, size_t idx, double v, float i
     reinterpret_cast<float*>(R)[idx] = (float)v;
   } else if constexpr (RF == RF_BF16) {
     reinterpret_cast<__nv_bfloat16*>(R)[idx] = __double2bfloat16(v);
+  } else if constexpr (RF == RF_F16) {
+    // in units of the column's power-of-two scale, saturating at 65504
+    const float x = fminf(fmaxf((float)(v * (double)inv_scale), -65504.0f), 65504.0f);
+    reinterpret_cast<__half*>(R)[idx] = __float2half_rn(x);
   } else {
     reinterpret_cast<__nv_fp8_e4m3*>(R)[idx] = __nv_fp8_e4m3((float)(v * (double)inv_scale));
   }
@@ -434,6 +438,7 @@ pide_status launch_prep(pide_ctx* c, const double* b, int B, int mode, const dou
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 2);
   if (emul && mode == 0 && rfmt == RF_BF16) return launch_prep_df_bf16(c, b, B, lift, track, st);
+  if (rfmt == RF_F16) return PIDE_EINVAL;   // FP16 right-hand sides: launch_prep_f16 (scales first)
   dim3 g = col_grid(c->n, B);
   double* cmb = c->colmax + c->ws_B;
   const int t = track ? 1 : 0;
@@ -463,14 +468,15 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
   const int t = track ? 1 : 0;
   if (emul && mode == 0 && R && !r_out && rfmt != RF_F64) {
     const pide_status s = launch_residual_df(c, b, u, B, lift, rfmt, R, c->ld,
-                                             rfmt == RF_E4M3 ? c->col_scale + col0 : nullptr, cm,
-                                             track, fl, st);
+                                             (rfmt == RF_E4M3 || rfmt == RF_F16) ? c->col_scale + col0 : nullptr,
+                                             cm, track, fl, st);
     if (s != PIDE_EUNSUPPORTED) return s;      // else: the FP64 stencil below
   }
   switch (rfmt) {
     case RF_F64: (c->dims == 3 ? residual_kernel<RF_F64, true> : residual_kernel<RF_F64, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     case RF_F32: (c->dims == 3 ? residual_kernel<RF_F32, true> : residual_kernel<RF_F32, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
     case RF_BF16: (c->dims == 3 ? residual_kernel<RF_BF16, true> : residual_kernel<RF_BF16, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, nullptr, r_out, cm, t, fl); break;
+    case RF_F16: (c->dims == 3 ? residual_kernel<RF_F16, true> : residual_kernel<RF_F16, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
     default: (c->dims == 3 ? residual_kernel<RF_E4M3, true> : residual_kernel<RF_E4M3, false>)<<<g, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), c->ld, mode, c->w, c->dinv, lift, R, c->col_scale + col0, r_out, cm, t, fl); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());
@@ -488,6 +494,7 @@ pide_status launch_residual_persistent(pide_ctx* c, const double* b, const doubl
   void* R = (uint8_t*)c->R + (size_t)col0 * c->ld * rhs_elem_bytes(rfmt);
   const int grid = c->num_sms * c->resid_ctas_per_sm;
   const float* cs = c->col_scale + col0;
+  if (rfmt == RF_F16) return PIDE_EUNSUPPORTED;
   switch (rfmt) {
     case RF_F32: (c->dims == 3 ? residual_flat_kernel<RF_F32, true> : residual_flat_kernel<RF_F32, false>)<<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;
     case RF_BF16: (c->dims == 3 ? residual_flat_kernel<RF_BF16, true> : residual_flat_kernel<RF_BF16, false>)<<<grid, 256, 0, st>>>(b, u, c->n, c->mx, plane_of(c), B, c->ld, mode, c->w, c->dinv, lift, R, nullptr, c->flags); break;

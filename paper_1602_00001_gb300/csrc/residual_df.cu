@@ -134,6 +134,9 @@ __device__ __forceinline__ void store_r(void* R, size_t idx, float s, float e, f
     reinterpret_cast<__nv_bfloat16*>(R)[idx] = bf16_of_pair(s, e);
   } else if constexpr (RF == RF_F32) {
     reinterpret_cast<float*>(R)[idx] = s;
+  } else if constexpr (RF == RF_F16) {
+    // isc a power of two: s * isc exact; saturating at 65504
+    reinterpret_cast<__half*>(R)[idx] = __float2half_rn(fminf(fmaxf(s * isc, -65504.0f), 65504.0f));
   } else {
     reinterpret_cast<__nv_fp8_e4m3*>(R)[idx] = __nv_fp8_e4m3(s * isc);
   }
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256, 2) residual_df_reg_kernel(
   float isc[DF_COLS], mxr[DF_COLS];
 #pragma unroll
   for (int k = 0; k < DF_COLS; ++k) {
-    isc[k] = (RF == RF_E4M3 && cbase + k < B) ? 1.0f / col_scale[cbase + k] : 1.0f;
+    isc[k] = ((RF == RF_E4M3 || RF == RF_F16) && cbase + k < B) ? 1.0f / col_scale[cbase + k] : 1.0f;
     mxr[k] = 0.f;
   }
   const int stride = DF_NR * gridDim.x * blockDim.x;
@@ -364,8 +367,8 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
     su[i] = make_float4(ha, hb, la, lb);
   }
   __syncthreads();
-  const float isa = (RF == RF_E4M3) ? 1.0f / col_scale[ca] : 1.0f;
-  const float isb = (RF == RF_E4M3 && has_b) ? 1.0f / col_scale[cb] : 1.0f;
+  const float isa = (RF == RF_E4M3 || RF == RF_F16) ? 1.0f / col_scale[ca] : 1.0f;
+  const float isb = ((RF == RF_E4M3 || RF == RF_F16) && has_b) ? 1.0f / col_scale[cb] : 1.0f;
   float mxa = 0.f, mxb = 0.f;
   const double* ba = b + (size_t)ca * n;
   const double* bb = b + (size_t)(has_b ? cb : ca) * n;
@@ -529,6 +532,13 @@ static pide_status launch_df_smem(pide_ctx* c, const double* b, const double* u,
       k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
       break;
     }
+    case RF_F16: {
+      auto k = residual_df_kernel<RF_F16, NR, DIM3>;
+      if (smem > 48 * 1024)
+        PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
+      break;
+    }
     default: {
       auto k = residual_df_kernel<RF_E4M3, NR, DIM3>;
       if (smem > 48 * 1024)
@@ -546,7 +556,7 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
                                const float* col_scale, double* colmax_r, bool track,
                                const uint32_t* flags, cudaStream_t st) {
   if (B == 0) return PIDE_OK;
-  if (rfmt != RF_BF16 && rfmt != RF_F32 && rfmt != RF_E4M3) return PIDE_EINVAL;
+  if (rfmt != RF_BF16 && rfmt != RF_F32 && rfmt != RF_E4M3 && rfmt != RF_F16) return PIDE_EINVAL;
   const int t = track ? 1 : 0;
   const bool three = c->dims == 3;
   // default (-1): 8 nodes per thread (16 in 3-D stages relatively less halo
@@ -582,6 +592,7 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   switch (rfmt) {
     case RF_BF16: residual_df_reg_kernel<RF_BF16, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
     case RF_F32: residual_df_reg_kernel<RF_F32, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
+    case RF_F16: residual_df_reg_kernel<RF_F16, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
     default: residual_df_reg_kernel<RF_E4M3, NR, COLS><<<g, 256, 0, st>>>(b, u, c->n, c->mx, B, ldr, wh, wl, c->w, lift, R, col_scale, colmax_r, t, flags); break;
   }
   PIDE_CUDA_TRY(cudaGetLastError());

@@ -77,6 +77,10 @@ __global__ void row_to_f64_kernel(const void* __restrict__ inv, const void* __re
         v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(inv)[e]);
         if (corr) v += (double)(float)corr[e] * (double)corr_scale[p];
         break;
+      case PIDE_FP16:
+        v = (double)__half2float(reinterpret_cast<const __half*>(inv)[e]) * (double)row_scale[p];
+        if (corr) v += (double)(float)corr[e] * (double)corr_scale[p];
+        break;
       default: {
         v = (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv)[e];
         if (inv_lo) v += (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv_lo)[e];
@@ -116,6 +120,8 @@ pide_status quantize_store(pide_ctx* c, const double* G, cudaStream_t st) {
       to_bf16_kernel<<<grid, 256, 0, st>>>((const double2*)G, (__nv_bfloat162*)c->inv, total / 2);
       c->store_bytes = total * sizeof(__nv_bfloat16);
       break;
+    case PIDE_FP16:
+      return quantize_store_f16(c, G, st);
     case PIDE_FP8:
     case PIDE_FP8X2:
       PIDE_CUDA_TRY(cudaMallocAsync(&c->inv, total, st));

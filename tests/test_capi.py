@@ -90,6 +90,49 @@ def test_oracle_bf16_correction_pins():
     assert np.all(np.max(np.abs(C[rows]), axis=1) == 448)
 
 
+def test_oracle_fp16_rounding_pins():
+    """round_fp16 against torch's float16 conversion of float32 values (normal
+    and subnormal range, ties), inside the finite range; saturation at 65504."""
+    import torch
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(8000) * 10.0 ** rng.uniform(-9, 4.7, 8000)).astype(np.float32)
+    x = np.clip(x, -65504, 65504).astype(np.float64)
+    ref = torch.from_numpy(x).to(torch.float32).to(torch.float16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_fp16(x), ref)
+    assert O.round_fp16(np.array([1.0 + 2.0 ** -11]))[0] == 1.0              # tie to even
+    assert O.round_fp16(np.array([1.0 + 3 * 2.0 ** -11]))[0] == 1.0 + 2.0 ** -9
+    assert O.round_fp16(np.array([2.0 ** -25]))[0] == 0.0                     # tie at the bottom
+    assert O.round_fp16(np.array([3 * 2.0 ** -25]))[0] == 2.0 ** -23
+    assert O.round_fp16(np.array([7e4, -1e9]))[0] == 65504.0
+    assert O.round_fp16(np.array([-1e9]))[0] == -65504.0
+
+
+def test_oracle_fp16_store_pins():
+    """Power-of-two row scales put each row's maximum in [2^14, 2^15); s Q is
+    within half an FP16 step of M (2^-11 relative) for entries above 2^-14 s;
+    an all-zero row has s = 1; column scales put maxima in [2^11, 2^12); the
+    correction term cuts the store's median error by more than 8x."""
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((30, 200)) * 10.0 ** rng.uniform(-7, 1, (30, 200))
+    M[5] = 0.0
+    s, Q = O.quantize_rows_fp16(M)
+    assert np.all(np.log2(s) == np.round(np.log2(s)))
+    mq = np.max(np.abs(Q), axis=1)
+    rows = [p for p in range(30) if p != 5]
+    assert np.all((mq[rows] >= 2 ** 14) & (mq[rows] <= 2 ** 15)) and s[5] == 1.0
+    err = np.abs(M - s[:, None] * Q)
+    normal = np.abs(M) >= 2.0 ** -14 * s[:, None]
+    assert np.all(err[normal] <= 2.0 ** -11 * np.abs(M[normal]))
+    t, R = O.quantize_cols_fp16(M[rows])
+    mr = np.max(np.abs(R), axis=1)
+    assert np.all((mr >= 2 ** 11) & (mr <= 2 ** 12))
+    s2, Q2, c, C = O.quantize_fp16_correction(M[rows])
+    e1 = np.abs(M[rows] - s2[:, None] * Q2)
+    e2 = np.abs(M[rows] - s2[:, None] * Q2 - c[:, None] * C)
+    nz = e1 > 0
+    assert np.median(e2[nz] / e1[nz]) < 1 / 8
+
+
 def test_oracle_e4m3_rounding_pins():
     """round_e4m3 against torch's float8_e4m3fn conversion of float32 values
     (normal and subnormal range, ties), inside the finite range."""
