@@ -35,13 +35,13 @@ WORKLOAD = "198^2 interior (200x200 nodes), Fourier-field eps, 16 moving charges
 
 
 # DRAM traffic (read + write) of one launch of the GEMM at this workload, from the
-# one-pass ncu capture summarised in profiles/gemm_tc2_bf16_198sq_b1024.md; valid
+# one-pass ncu capture summarised in profiles/gemm_tc2_fp16_198sq_b1024.md; valid
 # only for the kernel source it was taken on (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh).
-# Average over the BF16 launches of a step (first apply 4.59 GB, each refinement
-# apply 5.50 GB); the e4m3 correction GEMM (2.57 GB) is reported on its own.
-GEMM_TRAFFIC = {"sha1": "57664fab34368d4e28e04755133fc49c15164ab2", "bytes": 5.20e9,
-                "precision": "bf16_fp8", "batch": 1024, "nodes": 200, "sweeps": 2,
-                "corr_bytes": 2.57e9}
+# Average over the FP16 launches of a step (first apply 4.56 GB, the refinement
+# apply 6.67 GB); the e4m3 correction GEMM (2.78 GB) is reported on its own.
+GEMM_TRAFFIC = {"sha1": "25e9367602dc449bfa31febebb4f8937a235ac46", "bytes": 5.61e9,
+                "precision": "fp16_fp8", "batch": 1024, "nodes": 200, "sweeps": 1,
+                "corr_mask": 1, "corr_bytes": 2.78e9}
 
 
 def gemm_source_sha1():
@@ -349,9 +349,9 @@ def threed_workload(args):
     setup64 = s64.info().setup_ms
     s64.close()
     torch.cuda.empty_cache()
-    # 3-D: BF16 alone reaches the target in two sweeps, as the correction term does
-    # (34^3 nodes: 215k against 180k solves/s), so BF16 is the default there
-    prec = args.precision if args.precision in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") else "bf16"
+    # 3-D: FP16 alone reaches the target in one sweep (34^3 nodes: 348k solves/s;
+    # with the correction term 282k, BF16 215k in two sweeps), so FP16 is the default
+    prec = args.precision if args.precision in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") else "fp16"
     s = Solver3D(N, N, N, h, eps, prec)
     s.reserve(B)
     u = torch.empty_like(b)
@@ -376,7 +376,7 @@ def threed_workload(args):
     la, ams = prof["apply"]
     pk, pk_kind = peaks()
     achieved = 2.0 * n * n * B / (ams / la * 1e-3) / 1e12 if la else 0.0
-    line = {"metric": "RHS solves/s, 3-D 32^3 interior (34^3 nodes), B=1024, refined BF16/FP8 @1e-6",
+    line = {"metric": "RHS solves/s, 3-D 32^3 interior (34^3 nodes), B=1024, refined FP16/BF16/FP8 @1e-6",
             "value": B / (ms * 1e-3), "unit": "RHS solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
@@ -491,7 +491,7 @@ def main():
     ap.add_argument("--precision", default=None,
                     choices=["bf16", "bf16_fp8", "fp16", "fp16_fp8", "fp8x2", "fp32"],
                     help="stored format (default: fp16_fp8 for the 2-D apply and the adjoint, "
-                         "bf16 in 3-D)")
+                         "fp16 in 3-D)")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
@@ -713,7 +713,7 @@ def main():
     traffic_valid = (gemm_source_sha1() == GEMM_TRAFFIC["sha1"]
                      and args.precision == GEMM_TRAFFIC["precision"] and k == GEMM_TRAFFIC["sweeps"]
                      and B == GEMM_TRAFFIC["batch"] and NN == GEMM_TRAFFIC["nodes"]
-                     and tn["corr_mask"] == 2 and tn["gemm_2cta"] == 1
+                     and tn["corr_mask"] == GEMM_TRAFFIC["corr_mask"] and tn["gemm_2cta"] == 1
                      and tn["gemm_a_hint"] == 1 and tn["gemm_u_hint"] == 1)
     if traffic_valid:
         traffic = GEMM_TRAFFIC["bytes"]
