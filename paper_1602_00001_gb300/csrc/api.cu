@@ -481,7 +481,7 @@ extern "C" void pide_destroy(pide_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {h->sym, h->sym_lo, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
+  void* ptrs[] = {h->sym, h->sym_lo, h->sym_scale, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
                   h->corr, h->corr_scale, h->Rc, h->col_scale_c,
                   h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
   for (void* p : ptrs)

@@ -77,11 +77,12 @@ struct pide_ctx {
   int corr_mask = 2;                // applies that add it: bit 0 the first, bit k sweep k
   size_t store_bytes = 0;
   void* sym = nullptr;              // packed lower 128x128 BF16 tiles of S^-1, hi term (B = 1 apply)
-  void* sym_lo = nullptr;           // same layout, lo term bf16(S^-1 - hi)
+  void* sym_lo = nullptr;           // same layout, lo term fp16((S^-1 - hi) / sigma_p)
+  float* sym_scale = nullptr;       // [n] sigma_p: power-of-two scale of row p's lo term
   long long sym_tiles = 0;
   size_t sym_bytes = 0;
   float* dfl = nullptr;             // [n] d as float (x = D r formed on the fly)
-  float* ysum = nullptr;            // [n] FP32 accumulation of the symmetric apply
+  double* ysum = nullptr;           // [n] accumulation of the symmetric apply (FP64 atomics)
   bool tmA_ok = false;
   CUtensorMap tmA, tmA_lo;          // TMA maps over the stored inverse (tensor-core formats)
   CUtensorMap tmA_corr;             // over the correction term (PIDE_BF16_FP8)

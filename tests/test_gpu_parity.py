@@ -350,9 +350,10 @@ def test_overlapped_refinement(B):
 @pytest.mark.parametrize("nx,ny", [(40, 33), (131, 12), (12, 140), (3, 3)])
 def test_symv_single_apply_is_exact_contraction(nx, ny):
     """B = 1 through the packed lower triangle of S^-1 = L^-1 D^-1 (BF16 hi +
-    BF16 lo, 128 x 128 tiles; upper blocks are the transposes of the stored
-    lower ones) with x = D r formed in FP32: equals the FP64 contraction of the
-    same rounded operands up to FP32 accumulation."""
+    FP16 lo with a power-of-two scale per row, 128 x 128 tiles; upper blocks
+    are the transposes of the stored lower ones) with x = D r formed in FP32:
+    equals the FP64 contraction of the same rounded operands up to FP32
+    accumulation."""
     h = 1.0 / (max(nx, ny) - 1)
     eps = W.eps_lognormal(nx, ny, seed=nx + ny)
     b = _b(nx, ny, h, eps, 1, seed=5)
@@ -362,7 +363,8 @@ def test_symv_single_apply_is_exact_contraction(nx, ny):
     d = O.diagonal_d(nx, ny, eps)
     S = Linv / d[None, :]
     hi = O.round_bf16(S)
-    Sl = hi + O.round_bf16(S - hi)
+    sig = O.pow2_scale(np.max(np.abs(S - hi), axis=1), 15)
+    Sl = hi + sig[:, None] * O.round_fp16((S - hi) / sig[:, None])
     blk = np.arange(s.n) // 128
     lower = blk[:, None] >= blk[None, :]
     A = np.where(lower, Sl, Sl.T)
@@ -371,8 +373,25 @@ def test_symv_single_apply_is_exact_contraction(nx, ny):
     mag = np.abs(A) @ np.abs(x)
     err = np.abs(u[0] - ref)
     assert np.all(err <= 2e-5 * mag + 1e-300), float(np.max(err / mag))
-    # two terms: far closer to the exact inverse than one BF16 term
-    assert O.rel_error_eq6(u, (Linv @ b[0])[None, :]) < 5e-5
+    # two terms (~19 bits): one apply is already close to the exact solution
+    assert O.rel_error_eq6(u, (Linv @ b[0])[None, :]) < 5e-6
+
+
+def test_symv_one_apply_at_198sq():
+    """198^2 unknowns: the symmetric two-term store alone (no refinement sweep)
+    within 5e-7 of the FP64 GPU apply on a moving-charge right-hand side."""
+    nx = ny = 200
+    h = 1.0 / 199
+    eps = W.eps_fourier(nx, ny, h, seed=1)
+    rho = W.moving_charges(nx, ny, h, seed=5, steps=3)
+    s = _solver(nx, ny, h, eps, "fp16_fp8")
+    b = s.rhs_from_charge(torch.from_numpy(rho).cuda())
+    u = torch.stack([s.apply(b[k:k + 1], sweeps=0)[0] for k in range(3)])
+    s.close()
+    s64 = _solver(nx, ny, h, eps, "fp64")
+    u64 = s64.apply(b)
+    d = ((u - u64).abs().amax(dim=1) / u64.abs().amax(dim=1)).max().item()
+    assert d < 5e-7, d
 
 
 def test_symv_refined_matches_gemv():
