@@ -451,9 +451,11 @@ def formats_workload(args):
         ref = s64.apply(b)
         s64.close()
         row = {}
-        for prec in ["fp32", "bf16", "bf16_fp8", "bf16_fp8_every_sweep", "fp8", "fp8x2"]:
-            # bf16_fp8: the correction term in the first sweep (the default);
-            # bf16_fp8_every_sweep: in the first apply and every sweep
+        for prec in ["fp32", "bf16", "bf16_fp8", "bf16_fp8_every_sweep", "fp16", "fp16_fp8",
+                     "fp8", "fp8x2"]:
+            # bf16_fp8: the correction term in the first sweep (its default);
+            # bf16_fp8_every_sweep: in the first apply and every sweep;
+            # fp16_fp8: in the first apply (its default)
             s = Solver(N, N, h, eps, "bf16_fp8" if prec.startswith("bf16_fp8") else prec)
             if prec == "bf16_fp8_every_sweep":
                 s.set_tuning(corr_mask=(1 << 30) - 1)
