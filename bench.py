@@ -37,11 +37,11 @@ WORKLOAD = "198^2 interior (200x200 nodes), Fourier-field eps, 16 moving charges
 # DRAM traffic (read + write) of one launch of the GEMM at this workload, from the
 # one-pass ncu capture summarised in profiles/gemm_tc2_fp16_198sq_b1024.md; valid
 # only for the kernel source it was taken on (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh).
-# Average over the FP16 launches of a step (first apply 4.56 GB, the refinement
-# apply 6.67 GB); the e4m3 correction GEMM (2.78 GB) is reported on its own.
-GEMM_TRAFFIC = {"sha1": "25e9367602dc449bfa31febebb4f8937a235ac46", "bytes": 5.61e9,
+# Average over the FP16 launches of a step (first apply 5.69 GB, the refinement
+# apply 8.51 GB); the e4m3 correction GEMM (2.91 GB) is reported on its own.
+GEMM_TRAFFIC = {"sha1": "9e0a111ab3c4b31aceb2ff4c7fcfb63b402bc6d4", "bytes": 7.10e9,
                 "precision": "fp16_fp8", "batch": 1024, "nodes": 200, "sweeps": 1,
-                "corr_mask": 1, "corr_bytes": 2.78e9}
+                "corr_mask": 1, "corr_bytes": 2.91e9}
 
 
 def gemm_source_sha1():
@@ -673,10 +673,10 @@ def main():
     u_host = torch.empty((E_BATCHES * B, n), dtype=torch.float64).pin_memory()
     s.solve_stream(in_host, u_host, chunk=B, sweeps=k)          # allocates the device slots
     torch.cuda.synchronize()
-    # five timed calls; the median call is reported, every call's rate beside it
+    # seven timed calls; the median call is reported, every call's rate beside it
     # (host-side copy rates vary between calls on a shared machine)
     call_rates = []
-    for _ in range(5):
+    for _ in range(7):
         t0 = time.perf_counter()
         s.solve_stream(in_host, u_host, chunk=B, sweeps=k)
         dt = reduce_max((time.perf_counter() - t0) / E_BATCHES, dist)
