@@ -3,7 +3,9 @@
 
 One step = one refined apply of the whole batch: right-hand-side prep, the
 first tensor-core apply and k refinement sweeps (stencil residual + apply),
-inputs resident in HBM.  The e2e figure streams steps from pinned host memory
+inputs resident in HBM.  The default store is FP16 with power-of-two row
+scales plus an e4m3 correction term added in the first apply (--precision
+selects BF16, BF16 + e4m3, FP16, FP8 hi+lo or FP32).  The e2e figure streams steps from pinned host memory
 through pide_solve_stream (copies in and out inside the timed region).  k is the smallest sweep count whose Eq. (6)
 error against the plain FP64 GPU apply is <= 0.5e-6 on sampled columns
 (checked against the FP64 oracle on two columns as well).  The metric is

@@ -26,7 +26,7 @@ def test_noalloc_matches_apply_twice():
     n = 50
     h = 1.0 / (n - 1)
     eps = W.eps_fourier(n, n, h, seed=1)
-    for prec, B in (("bf16", 5), ("fp32", 8), ("fp64", 1)):
+    for prec, B in (("bf16", 5), ("fp16", 3), ("fp32", 8), ("fp64", 1)):
         s = binding.Solver(n, n, h, eps, prec)
         b = torch.from_numpy(O.rhs_from_charge(n, n, h, eps, W.gaussian_blobs(n, n, h, 9, batch=B))).cuda()
         # the scratch right-hand side is FP32: two FP64-residual sweeps take the
