@@ -127,10 +127,11 @@ typedef struct {
  *             finite and > 0 (NULL means eps = 1, the case of Eq. 2).
  *   p         storage format of the inverse.  The inverse is always formed
  *             in FP64 on the GPU (block-tridiagonal elimination), then
- *             quantised; the FP64 copy is kept only for PIDE_FP64.  BF16
- *             handles also keep the lower triangle of the symmetric S^-1 in
- *             128 x 128 tiles of two BF16 terms (hi + lo, the size of the
- *             one-term L^-1) for one-column applies.
+ *             quantised; the FP64 copy is kept only for PIDE_FP64.  BF16 and
+ *             FP16 handles (with or without the correction term) also keep
+ *             the lower triangle of the symmetric S^-1 in 128 x 128 tiles of
+ *             two terms (BF16 hi + FP16 lo with a power-of-two scale per row,
+ *             the size of the one-term L^-1) for one-column applies.
  *   stream    cudaStream_t for all setup work (the call synchronises it).
  *   out       receives the new handle (NULL on failure).
  * Errors: EINVAL (bad grid, eps), ENOMEM, ECUDA, EUNSUPPORTED (not sm_103).
@@ -338,13 +339,14 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           phase (measured faster on GB300: the two overlapped kernels
  *                           slow each other by more than the residual's time)
  *   PIDE_TUNE_RESID_CTAS    residual CTAs (256 threads) per SM while overlapped: 1..8 (default 2)
- *   PIDE_TUNE_SYMV          1 (default): BF16 handles apply B = 1 through the packed lower
- *                           triangle of the symmetric S^-1 (L^-1 = S^-1 D) in two BF16 terms,
- *                           ~16 significant bits for the bytes of the one-term L^-1, so
- *                           refinement needs about a quarter of the sweeps;
+ *   PIDE_TUNE_SYMV          1 (default): BF16 and FP16 handles apply B = 1 through the packed
+ *                           lower triangle of the symmetric S^-1 (L^-1 = S^-1 D) in two terms
+ *                           (BF16 hi + row-scaled FP16 lo), ~19 significant bits for the bytes
+ *                           of the one-term L^-1, summed in FP32 within 8 tiles and FP64
+ *                           across them: one apply reaches ~5e-7 at 198^2 unknowns;
  *                           0: through the one-term L^-1 (GEMV)
- *   PIDE_TUNE_RESID_EMUL    1 (default): BF16 / FP8 / FP8X2 handles evaluate the refinement
- *                           residual (forward mode, and the BF16 prep) on the integer and
+ *   PIDE_TUNE_RESID_EMUL    1 (default): BF16 / FP16 / FP8 / FP8X2 handles evaluate the
+ *                           refinement residual (forward mode, and the BF16 prep) on the integer and
  *                           FP32 pipes: each FP64 input split into two floats (47
  *                           significant bits), the stencil in error-free float arithmetic,
  *                           absolute error ~2^-45 (|u_p| + sum_q w_pq |u_q|); skipped when
