@@ -147,3 +147,23 @@ def test_oracle_e4m3_rounding_pins():
     assert O.round_e4m3(np.array([1.1875]))[0] == 1.25
     assert O.round_e4m3(np.array([2.0 ** -10]))[0] == 0.0          # ties to even at the bottom
     assert O.round_e4m3(np.array([3 * 2.0 ** -10]))[0] == 2.0 ** -8
+
+
+def _header_enum(name):
+    """{enumerator: value} of `typedef enum {...} name;` in include/pide.h."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "include", "pide.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef enum \{([^}]*)\}\s*" + name + ";", src).group(1)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"(PIDE_\w+)\s*=\s*(\d+)", body)}
+
+
+def test_binding_precisions_and_tuning_keys_match_the_header():
+    """The binding's precision names and tuning keys carry the header's values."""
+    from paper_1602_00001_gb300 import binding
+    prec = _header_enum("pide_precision")
+    assert {("PIDE_" + k.upper()): v for k, v in binding.PRECISIONS.items()} == prec
+    keys = _header_enum("pide_tune_key")
+    assert {("PIDE_TUNE_" + k.upper()): v for k, v in binding.Solver.TUNE_KEYS.items()} == keys
