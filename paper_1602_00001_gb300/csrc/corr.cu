@@ -92,12 +92,20 @@ __global__ void corr_rhs_kernel(const T2* __restrict__ R, int n, int ld,
   const int j = blockIdx.x;
   const T2* r2 = R + (size_t)j * (ld / 2);
   const int half = ld / 2;                 // ld is a multiple of 64
+  // 16-byte loads: four pairs per thread and step
+  const uint4* r8 = reinterpret_cast<const uint4*>(r2);
   float mx = 0.0f;
-  for (int q = threadIdx.x; q < half; q += blockDim.x) {
-    float2 v = to_float2<T2>(r2[q]);
-    if (2 * q >= n) v.x = 0.0f;
-    if (2 * q + 1 >= n) v.y = 0.0f;
-    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  for (int q4 = threadIdx.x; q4 < half / 4; q4 += blockDim.x) {
+    const uint4 raw = r8[q4];
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = 4 * q4 + i;
+      float2 v = to_float2<T2>(*reinterpret_cast<const T2*>(&w[i]));
+      if (2 * q >= n) v.x = 0.0f;
+      if (2 * q + 1 >= n) v.y = 0.0f;
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
   }
   mx = block_max_f(mx, red);
   const float t = mx > 0.0f ? (float)((double)mx / 448.0) : 1.0f;
@@ -105,11 +113,20 @@ __global__ void corr_rhs_kernel(const T2* __restrict__ R, int n, int ld,
   const float isc = 1.0f / t;
   __nv_fp8x2_e4m3* o2 = reinterpret_cast<__nv_fp8x2_e4m3*>(
       reinterpret_cast<uint8_t*>(Rc) + (size_t)j * ld);
-  for (int q = threadIdx.x; q < half; q += blockDim.x) {
-    float2 v = to_float2<T2>(r2[q]);
-    if (2 * q >= n) v.x = 0.0f;
-    if (2 * q + 1 >= n) v.y = 0.0f;
-    o2[q] = __nv_fp8x2_e4m3(make_float2(v.x * isc, v.y * isc));
+  for (int q4 = threadIdx.x; q4 < half / 4; q4 += blockDim.x) {
+    const uint4 raw = r8[q4];
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+    uint16_t o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = 4 * q4 + i;
+      float2 v = to_float2<T2>(*reinterpret_cast<const T2*>(&w[i]));
+      if (2 * q >= n) v.x = 0.0f;
+      if (2 * q + 1 >= n) v.y = 0.0f;
+      o[i] = __nv_fp8x2_e4m3(make_float2(v.x * isc, v.y * isc)).__x;
+    }
+    reinterpret_cast<uint2*>(o2)[q4] = make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                                                  (uint32_t)o[2] | ((uint32_t)o[3] << 16));
   }
 }
 

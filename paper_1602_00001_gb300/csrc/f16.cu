@@ -110,8 +110,20 @@ __global__ void prep_f16_kernel(const double* __restrict__ b, int n, int ldr, in
     col_scale[col] = ldexpf(1.0f, k);
     if (track) colmax_b[col] = __longlong_as_double((long long)mx);
   }
-  for (int p = threadIdx.x; p < n; p += blockDim.x)
-    R[(size_t)col * ldr + p] = __ushort_as_half(f16_bits_scaled(rhs_value(bc, p, mode, dinv, lift), k));
+  // second pass (from L2), again four loads in flight per thread
+  for (int p0 = threadIdx.x; p0 < n; p0 += step) {
+    double v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = p0 + i * blockDim.x;
+      v[i] = p < n ? rhs_value(bc, p, mode, dinv, lift) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = p0 + i * blockDim.x;
+      if (p < n) R[(size_t)col * ldr + p] = __ushort_as_half(f16_bits_scaled(v[i], k));
+    }
+  }
 }
 
 }  // namespace
