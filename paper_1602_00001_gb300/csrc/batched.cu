@@ -49,7 +49,12 @@ constexpr int SB_OUT = 8192;
 constexpr int SB_TMMAX = 512;
 constexpr int SB_APAD = SB_TMMAX + 4;
 constexpr int SB_XPAD = 64 + 4;
-constexpr size_t SB_SMEM = (size_t)(2 * SB_K * SB_APAD + 2 * SB_K * SB_XPAD) * sizeof(float);
+// FP32 problems stage A row-major through asynchronous copies instead:
+// [TM][SB_APITCH] per stage (16 K values and 4 of padding per row).
+constexpr int SB_APITCH = SB_K + 4;
+constexpr int SB_A_FLOATS = (2 * SB_K * SB_APAD > 2 * SB_TMMAX * SB_APITCH)
+                                ? 2 * SB_K * SB_APAD : 2 * SB_TMMAX * SB_APITCH;
+constexpr size_t SB_SMEM = (size_t)(SB_A_FLOATS + 2 * SB_K * SB_XPAD) * sizeof(float);
 
 __device__ __forceinline__ int sb_tn(int code) { return code == 0 ? 16 : (code == 1 ? 32 : 64); }
 
@@ -164,13 +169,124 @@ __device__ __forceinline__ void simt_tile(const BatchProb& P, int p0, int c0, in
   }
 }
 
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The same tile for an FP32 problem, A staged without a register round trip:
+// 16-byte asynchronous copies into a row-major [TM][SB_APITCH] tile (zero-fill
+// past n), read back with one 16-byte shared load per row and four K values.
+// The thread's 8 rows are rg + RG i (RG = TM / 8), so that the 8 rows a warp
+// reads at once are consecutive: stride 20 floats puts them in 8 distinct
+// 4-bank groups.  No transposed scalar stores (the SIMT tile's main cost).
+template <int TN>
+__device__ __forceinline__ void simt_tile_async(const BatchProb& P, int p0, int c0, int accumulate,
+                                                float* __restrict__ sA, float* __restrict__ sX) {
+  constexpr int TM = SB_OUT / TN;
+  constexpr int CG = TN / 4;
+  constexpr int RG = TM / 8;
+  constexpr int AC = TM * 4 / 256;       // 16-byte chunks of A per thread and K step
+  const int t = threadIdx.x;
+  const int cg = t % CG, rg = t / CG;
+  const int ncols = min(TN, P.B - c0);
+  const float* inv = reinterpret_cast<const float*>(P.inv);
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float4 rx = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool xloader = t < TN * 4;
+  const int xc = t >> 2, xk = (t & 3) * 4;
+  auto issue_a = [&](int k0, int buf) {
+    float* A = sA + buf * TM * SB_APITCH;
+#pragma unroll
+    for (int q = 0; q < AC; ++q) {
+      const int c = t + 256 * q;
+      const int r = c >> 2, kq = c & 3;
+      const int gp = p0 + r, gk = k0 + kq * 4;
+      int bytes = 0;
+      const float* src = inv;
+      if (gp < P.n && gk < P.n) {
+        bytes = 4 * min(4, P.n - gk);
+        src = inv + (size_t)gp * P.ld + gk;
+      }
+      cp_async16(A + r * SB_APITCH + kq * 4, src, bytes);
+    }
+    cp_async_commit();
+  };
+  auto store_x = [&](int buf) {
+    if (xloader) {
+      float* X = sX + buf * SB_K * SB_XPAD;
+      X[(xk + 0) * SB_XPAD + xc] = rx.x;
+      X[(xk + 1) * SB_XPAD + xc] = rx.y;
+      X[(xk + 2) * SB_XPAD + xc] = rx.z;
+      X[(xk + 3) * SB_XPAD + xc] = rx.w;
+    }
+  };
+  const int nk = (P.n + SB_K - 1) / SB_K;
+  issue_a(0, 0);
+  if (xloader) rx = load_x4(P, c0 + xc, xc < ncols, xk);
+  store_x(0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int ks = 0; ks < nk; ++ks) {
+    const int buf = ks & 1;
+    if (ks + 1 < nk) {
+      issue_a((ks + 1) * SB_K, buf ^ 1);
+      if (xloader) rx = load_x4(P, c0 + xc, xc < ncols, (ks + 1) * SB_K + xk);
+    }
+    const float* A = sA + buf * TM * SB_APITCH + rg * SB_APITCH;
+    const float* X = sX + buf * SB_K * SB_XPAD + cg * 4;
+#pragma unroll
+    for (int kq = 0; kq < 4; ++kq) {
+      float4 a[8], x[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        a[i] = *reinterpret_cast<const float4*>(A + i * RG * SB_APITCH + kq * 4);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        x[kk] = *reinterpret_cast<const float4*>(X + (kq * 4 + kk) * SB_XPAD);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const float xv[4] = {x[kk].x, x[kk].y, x[kk].z, x[kk].w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float av = kk == 0 ? a[i].x : (kk == 1 ? a[i].y : (kk == 2 ? a[i].z : a[i].w));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av, xv[j], acc[i][j]);
+        }
+      }
+    }
+    if (ks + 1 < nk) store_x(buf ^ 1);
+    cp_async_wait_all();
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = cg * 4 + j;
+    if (c >= ncols) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int p = p0 + rg + RG * i;
+      if (p >= P.n) continue;
+      double* dst = P.u + (size_t)(c0 + c) * P.n + p;
+      *dst = accumulate ? *dst + (double)acc[i][j] : (double)acc[i][j];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __restrict__ probs,
                                                             const int4* __restrict__ items,
                                                             int nitems, int* __restrict__ counter,
-                                                            int accumulate, int phase) {
+                                                            int accumulate, int phase, int sb_async) {
   extern __shared__ float sb_smem[];
   float* sA = sb_smem;
-  float* sX = sb_smem + 2 * SB_K * SB_APAD;
+  float* sX = sb_smem + SB_A_FLOATS;
   __shared__ int s_item;
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -183,7 +299,11 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
     if (phase > P.pad) continue;                      // this problem already ran its sweeps
     const int tn = sb_tn(w.w);
     const int p0 = w.y * (SB_OUT / tn), c0 = w.z * tn;
-    if (w.w == 0) simt_tile<16>(P, p0, c0, accumulate, sA, sX);
+    if (P.fmt == 0 && sb_async) {
+      if (w.w == 0) simt_tile_async<16>(P, p0, c0, accumulate, sA, sX);
+      else if (w.w == 1) simt_tile_async<32>(P, p0, c0, accumulate, sA, sX);
+      else simt_tile_async<64>(P, p0, c0, accumulate, sA, sX);
+    } else if (w.w == 0) simt_tile<16>(P, p0, c0, accumulate, sA, sX);
     else if (w.w == 1) simt_tile<32>(P, p0, c0, accumulate, sA, sX);
     else simt_tile<64>(P, p0, c0, accumulate, sA, sX);
   }
@@ -577,7 +697,7 @@ static pide_status batch_apply(pide_batch* p, int phase, cudaStream_t st) {
     PIDE_CUDA_TRY(cudaFuncSetAttribute(batched_apply_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SB_SMEM));
     batched_apply_kernel<<<grid_apply, 256, SB_SMEM, st>>>(p->d_probs, p->d_items, p->nitems,
-                                                           p->d_counter + phase, phase > 0, phase);
+                                                           p->d_counter + phase, phase > 0, phase, 1);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
   if (p->ngitems > 0) {
