@@ -23,6 +23,11 @@ of Partial Integro-Differential Equations"):
 * Table 1's experiment: round the entries of the inverse to k decimals.
 * The adjoint of u = L(eps)^-1 b (not in the paper; the gradient formula is
   derived here from differentiating L u = b, see ``adjoint_gradients``).
+* The stored formats of the inverse written out (not in the paper, which
+  rounds to decimals): bfloat16, float32, e4m3 and binary16 rounding, and the
+  quantisers built on them (per-row e4m3 scales, power-of-two FP16 row and
+  column scales, the e4m3 correction term of a BF16 or FP16 store), so that
+  tests can form the exact product of the GPU's own roundings.
 
 Precision: float64 throughout.  Loops are plain Python over one index with
 numpy vector operations inside; there is no blocking or reordering beyond the
@@ -32,7 +37,9 @@ Pins (tests/test_oracle.py): Fig. 3 bit-exact, Table 1 (24 of 25 cells),
 the 2-D discrete sine transform closed form at eps = 1, second-order
 convergence on a manufactured solution with smooth eps, symmetry of D*L,
 nonnegativity of L^-1, brute force against LAPACK on tiny grids,
-banded-vs-dense agreement, and central finite differences for the adjoint.
+banded-vs-dense agreement, and central finite differences for the adjoint;
+the roundings against torch's conversions and exact ties, the quantisers by
+their error bounds and scale ranges (tests/test_capi.py).
 """
 from __future__ import annotations
 
