@@ -107,6 +107,25 @@ def test_oracle_fp16_rounding_pins():
     assert O.round_fp16(np.array([-1e9]))[0] == -65504.0
 
 
+def test_oracle_fp16_rounding_direct_from_double():
+    """round_fp16 rounds once, from the FP64 value (as the GPU's integer
+    conversion does): it equals numpy's direct float64 -> float16 conversion,
+    including values one FP64 ulp either side of an FP16 tie, where a detour
+    through float32 would round twice."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(100000) * 10.0 ** rng.uniform(-9, 4.7, 100000)
+    x = x[np.abs(x) < 65504]
+    assert np.array_equal(O.round_fp16(x), x.astype(np.float16).astype(np.float64))
+    ties = np.array([1.0 + 2.0 ** -11, 3.0 + 1.5 * 2.0 ** -10, 2.0 ** -20 + 2.0 ** -25,
+                     5 * 2.0 ** -16 + 2.0 ** -25])
+    near = np.concatenate([ties, np.nextafter(ties, np.inf), np.nextafter(ties, -np.inf), -ties])
+    assert np.array_equal(O.round_fp16(near), near.astype(np.float16).astype(np.float64))
+    # the float32 detour differs on the ulp-above cases (a double-rounding witness)
+    up = np.nextafter(ties[:1], np.inf)
+    assert O.round_fp16(up)[0] == 1.0 + 2.0 ** -10
+    assert O.round_fp16(O.round_fp32(up))[0] == 1.0
+
+
 def test_oracle_fp16_store_pins():
     """Power-of-two row scales put each row's maximum in [2^14, 2^15); s Q is
     within half an FP16 step of M (2^-11 relative) for entries above 2^-14 s;
