@@ -712,6 +712,8 @@ def main():
     else:
         peak_tf = pk["bf16_tflops_sustained"]
         peak_src = f"{pk_kind} bf16_tflops_sustained"
+        if args.precision.startswith("fp16"):
+            peak_src += " (FP16 and BF16 share the dense tensor rate: nominal ratio 1)"
     traffic = None
     tn = s.get_tuning()
     traffic_valid = (gemm_source_sha1() == GEMM_TRAFFIC["sha1"]
