@@ -212,8 +212,12 @@ static pide_status solve_overlapped(pide_ctx* c, const double* b, int mode, cons
 }
 
 // L x = f with x = Q(L^-1) q(f), then `sweeps` refinement sweeps
-// x += Q(L^-1) q(f - L x), the residual in FP64.  mode 0: f = b + lift (Eq. 3);
-// mode 1 (adjoint): f = b / d, so that x = L^-1 D^-1 b = S^-1 b.
+// x += Q(L^-1) q(f - L x), the residual in FP64 (or double-float).  mode 0:
+// f = b + lift (Eq. 3); mode 1 (adjoint): f = b / d, so that
+// x = L^-1 D^-1 b = S^-1 b.  With an e4m3 correction term, apply k (0: the
+// first, k: sweep k) adds C e4m3(q(r)) when bit k of corr_mask is set.  FP16
+// right-hand sides take their power-of-two column scales once, from f, in the
+// prep; every residual of the solve reuses them.
 static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, double* x,
                            int B, int sweeps, double tol, cudaStream_t st) {
   PIDE_TRY(ensure_workspace(c, B));
