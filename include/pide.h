@@ -166,8 +166,12 @@ void pide_destroy(pide_handle h);
 /*
  * pide_apply -- step 3 with iterative refinement:
  *   u = Q(L^-1) b;  then up to max_sweeps times  u += Q(L^-1) (b - L u),
- * where Q(.) is the stored inverse and the residual b - L u is taken in FP64
- * with the 5-point stencil of Eq. (3).
+ * where Q(.) is the stored inverse (with the e4m3 correction term added in
+ * the applies PIDE_TUNE_CORR_MASK selects, for the *_FP8 stores) and the
+ * residual b - L u is taken to FP64 accuracy (FP64 stencil, or double-float
+ * on the integer/FP32 pipes) with the 5-point stencil of Eq. (3).  The
+ * residual reaches the tensor cores in the store's right-hand-side format
+ * (BF16; FP16 with the column scales of b; e4m3 with per-column scales).
  *   b_dev     [B][n] right-hand sides (Eq. 3 form, interior nodes).
  *   u_dev     [B][n] solutions (written; must not alias b_dev).
  *   B         number of right-hand sides, >= 0 (0 is a no-op).
