@@ -75,8 +75,11 @@ typedef enum {
                        column scales t_j set once per apply from the first right-hand side
                        (column maximum in [2^11, 2^12)), tensor-core apply on the FP16 pipe
                        (the BF16 rate) with u += s_p t_j acc: 11 significant bits where BF16
-                       has 8.  B = 1 uses the symmetric two-term BF16 store as PIDE_BF16 does;
-                       not served by the batched entry points */
+                       has 8.  The scales are kept in FP32's normal range: a right-hand-side
+                       column whose largest |f| lies above ~2^139 saturates at 65504 and one
+                       below ~2^-115 loses bits to FP16 subnormals.  B = 1 uses the symmetric
+                       two-term store as PIDE_BF16 does; not served by the batched entry
+                       points */
   PIDE_FP16_FP8 = 7 /* PIDE_FP16 plus the e4m3 correction term of PIDE_BF16_FP8, taken against
                        the FP16 store; PIDE_TUNE_CORR_MASK defaults to 1 (the first apply) */
 } pide_precision;
