@@ -165,6 +165,17 @@ def test_b1_adjoint_and_tolerance():
     assert O.rel_error_eq6(ut.cpu().numpy(), O.solve(nx, ny, eps, b, route="band")) < 1e-8
 
 
+def test_b1_gemv_over_the_fp16_store():
+    """B = 1 through the one-term FP16 store (symv off: the GEMV with the row
+    scales, FP32 right-hand side), refined to the oracle."""
+    nx, ny, h, eps = _grid()
+    b = _b(nx, ny, h, eps, 1, seed=23)
+    s = _solver(nx, ny, h, eps, "fp16")
+    s.set_tuning(symv=0)
+    u = s.apply(b, sweeps=3).cpu().numpy()
+    assert O.rel_error_eq6(u, O.solve(nx, ny, eps, b, route="band")) < 1e-6
+
+
 @pytest.mark.parametrize("prec", ["fp16", "fp16_fp8"])
 def test_save_load(prec, tmp_path):
     from paper_1602_00001_gb300.binding import Solver
