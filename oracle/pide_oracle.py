@@ -33,13 +33,19 @@ Precision: float64 throughout.  Loops are plain Python over one index with
 numpy vector operations inside; there is no blocking or reordering beyond the
 textbook algorithms named above.
 
-Pins (tests/test_oracle.py): Fig. 3 bit-exact, Table 1 (24 of 25 cells),
-the 2-D discrete sine transform closed form at eps = 1, second-order
-convergence on a manufactured solution with smooth eps, symmetry of D*L,
-nonnegativity of L^-1, brute force against LAPACK on tiny grids,
-banded-vs-dense agreement, and central finite differences for the adjoint;
-the roundings against torch's conversions and exact ties, the quantisers by
-their error bounds and scale ranges (tests/test_capi.py).
+Pins (tests/test_oracle.py): Fig. 3 bit-exact, Table 1 (24 of 25 cells,
+which also pins Eq. (6): ``table1_row`` measures its error through
+``rel_error_eq6``), a hand-computed multi-column Eq. (6) case whose worst
+column is not the one with the largest |u|, the 2-D discrete sine transform
+closed form at eps = 1, second-order convergence on a manufactured solution
+with smooth eps, symmetry of D*L, nonnegativity of L^-1, brute force against
+LAPACK on tiny grids, banded-vs-dense agreement, and central finite
+differences for the adjoint; the roundings against torch's conversions and
+exact ties, the quantisers by their error bounds and scale ranges, the
+two-term e4m3 quantiser by its 2^-8 error bound, the range of its lo term and
+lo = 0 on rows exact in e4m3 (tests/test_capi.py).  tests/test_oracle_pins.py
+plants plausible mistakes in copies of Eq. (6) and of the two-term quantiser
+and checks that these pins reject every one of them.
 """
 from __future__ import annotations
 
@@ -415,7 +421,8 @@ def table1_row(n: int, digits_list, route: str = "auto"):
         M = Linv if digits is None else round_decimals(Linv, digits)
         u = np.zeros((n, n))
         u[1:-1, 1:-1] = (M @ b).reshape(n - 2, n - 2)
-        out.append(float(np.max(np.abs(ua - u)) / np.max(np.abs(ua))))
+        # Eq. (6) over every node of the grid (boundary nodes carry u = 0 on both sides)
+        out.append(rel_error_eq6(u.reshape(-1), ua.reshape(-1)))
     return out
 
 

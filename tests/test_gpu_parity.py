@@ -378,11 +378,13 @@ def test_symv_single_apply_is_exact_contraction(nx, ny):
 
 
 def test_symv_one_apply_at_198sq():
-    """198^2 unknowns: the symmetric two-term store alone (no refinement sweep)
-    within 5e-7 of the FP64 GPU apply on a moving-charge right-hand side."""
+    """198^2 unknowns: the symmetric two-term store alone (no refinement sweep),
+    as the benchmark's B = 1 figure runs it (its operator: Fourier eps seed 5,
+    moving charges seed 5), within 5e-7 of the FP64 GPU apply on three
+    right-hand sides and within 1e-6 of the oracle on two of them."""
     nx = ny = 200
     h = 1.0 / 199
-    eps = W.eps_fourier(nx, ny, h, seed=1)
+    eps = W.eps_fourier(nx, ny, h, seed=5)
     rho = W.moving_charges(nx, ny, h, seed=5, steps=3)
     s = _solver(nx, ny, h, eps, "fp16_fp8")
     b = s.rhs_from_charge(torch.from_numpy(rho).cuda())
@@ -392,6 +394,8 @@ def test_symv_one_apply_at_198sq():
     u64 = s64.apply(b)
     d = ((u - u64).abs().amax(dim=1) / u64.abs().amax(dim=1)).max().item()
     assert d < 5e-7, d
+    ref = O.solve(nx, ny, eps, b[:2].cpu().numpy(), route="band")
+    assert O.rel_error_eq6(u[:2].cpu().numpy(), ref) < 1e-6
 
 
 def test_symv_refined_matches_gemv():
