@@ -3,13 +3,17 @@
 
 One step = one refined apply of the whole batch: right-hand-side prep, the
 first tensor-core apply and k refinement sweeps (stencil residual + apply),
-inputs resident in HBM.  The default store is FP16 with power-of-two row
-scales plus an e4m3 correction term added in the first apply (--precision
-selects BF16, BF16 + e4m3, FP16, FP8 hi+lo or FP32).  The e2e figure streams steps from pinned host memory
-through pide_solve_stream (copies in and out inside the timed region).  k is the smallest sweep count whose Eq. (6)
-error against the plain FP64 GPU apply is <= 0.5e-6 on sampled columns
-(checked against the FP64 oracle on two columns as well).  The metric is
-right-hand-side solves per second, whole job (all ranks).
+inputs resident in HBM.  The store is chosen by the library from the
+refinement's measured contraction (pide_setup_auto with its built-in probes,
+target 0.5e-6; on GB300 this picks FP16 with power-of-two row scales plus an
+e4m3 correction term added in the first apply); --precision forces BF16,
+BF16 + e4m3, FP16, FP16 + e4m3, FP8 hi+lo or FP32.  The e2e figure streams
+steps from pinned host memory through pide_solve_stream (copies in and out
+inside the timed region).  k is the smallest sweep count whose Eq. (6) error
+against the plain FP64 GPU apply is <= 0.5e-6 on sampled columns (checked
+against the FP64 oracle on two columns as well); the sweep count the library
+measured is reported beside it.  The metric is right-hand-side solves per
+second, whole job (all ranks).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -29,16 +33,17 @@ sys.path.insert(0, ROOT)
 
 NODES = 200                  # grid nodes per side (Eq. 2), 198^2 interior unknowns
 BATCH = 1024                 # right-hand sides per step
-PRECISION = "fp16_fp8"
+PRECISION = "auto"
 METRIC = "RHS solves/s at 198^2 grid, B=1 and 1024, refined BF16/FP8 vs FP64 apply @1e-6"
 UNIT = "RHS solves/s"
 TARGET_ERR = 0.5e-6          # calibration target (the bar is 1e-6)
 WORKLOAD = "198^2 interior (200x200 nodes), Fourier-field eps, 16 moving charges, B=1024"
 
 
-# DRAM traffic (read + write) of one launch of the GEMM at this workload, from the
-# one-pass ncu capture summarised in profiles/gemm_tc2_fp16_198sq_b1024.md; valid
-# only for the kernel source it was taken on (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh).
+# DRAM traffic (read + write) of one launch of the GEMM at this workload, from a
+# one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the SM-pair
+# GEMM launches of a timed step); valid only for the kernel source it was taken on
+# (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh), and reported as a stored figure.
 # Average over the FP16 launches of a step (first apply 5.69 GB, the refinement
 # apply 8.51 GB); the e4m3 correction GEMM (2.91 GB) is reported on its own.
 GEMM_TRAFFIC = {"sha1": "9e0a111ab3c4b31aceb2ff4c7fcfb63b402bc6d4", "bytes": 7.10e9,
@@ -140,49 +145,144 @@ def whole_job_rate(world: int, per_rank_batch: int, steps: int, ms_total_max: fl
     return world * per_rank_batch * steps / (ms_total_max / 1e3)
 
 
-def cpu_oracle_rate(nx, ny, h, eps, b_np, cols, factor=None):
-    """Oracle (numpy band LU) solves/s on a bounded sample of columns.
-    Returns (solves_per_s, seconds, factor_object, solution)."""
+# BLAS / OpenMP thread counts of the host processes that time the oracle
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _cpu_band_worker(nodes, seed, cols, col0, reps, warm, barrier, out_q):
+    """One host process: the oracle's band-LU factorisation of the workload's
+    operator (untimed, setup), then `reps` timed band solves of `cols` of its
+    columns, started together with the other processes."""
     from oracle import pide_oracle as O
-    if factor is None:
-        factor = O.BandSolver(nx, ny, eps)
+    from paper_1602_00001_gb300 import workloads as W
+    h = 1.0 / (nodes - 1)
+    eps = W.eps_fourier(nodes, nodes, h, seed=seed)
+    rho = W.moving_charges(nodes, nodes, h, seed=seed, steps=BATCH)[col0:col0 + cols]
+    b = O.rhs_from_charge(nodes, nodes, h, eps, rho)
+    fac = O.BandSolver(nodes, nodes, eps)
+    for _ in range(warm):
+        fac.solve(b)
+    barrier.wait()
     t = time.perf_counter()
-    u = factor.solve(b_np[:cols])
-    dt = time.perf_counter() - t
-    return cols / dt, dt, factor, u
+    u = None
+    for _ in range(max(reps, 1)):
+        u = fac.solve(b)
+    out_q.put((col0, time.perf_counter() - t, u if col0 == 0 else None))
+
+
+def _cpu_dense_worker(nodes, seed, out_q):
+    """One host process: the oracle's dense FP64 inverse of a grid that fits
+    host memory (formed untimed), then its dense apply (numpy/BLAS with the
+    thread count of this process's environment) at B = 1 and B = 64."""
+    from oracle import pide_oracle as O
+    from paper_1602_00001_gb300 import workloads as W
+    h = 1.0 / (nodes - 1)
+    eps = W.eps_fourier(nodes, nodes, h, seed=seed)
+    Linv = O.interior_inverse(nodes, nodes, eps, route="band")
+    b = O.rhs_from_charge(nodes, nodes, h, eps,
+                          W.moving_charges(nodes, nodes, h, seed=seed, steps=64))
+    out = {}
+    for B in (1, 64):
+        O.apply_inverse(Linv, b[:B])
+        reps, t = 0, time.perf_counter()
+        while time.perf_counter() - t < 1.0 or reps < 3:
+            O.apply_inverse(Linv, b[:B])
+            reps += 1
+        out[B] = B * reps / (time.perf_counter() - t)
+    out_q.put(out)
+
+
+def _spawn_with_threads(threads, target, args_list, timeout=900):
+    """Run target(*args, barrier, queue) (or target(*args, queue)) in fresh
+    spawned processes whose BLAS/OpenMP pools have `threads` threads; returns
+    the queued results."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in THREAD_VARS}
+    for k in THREAD_VARS:
+        os.environ[k] = str(threads)
+    try:
+        q = ctx.Queue()
+        barrier = ctx.Barrier(len(args_list)) if target is _cpu_band_worker else None
+        procs = []
+        for a in args_list:
+            extra = (barrier, q) if barrier is not None else (q,)
+            procs.append(ctx.Process(target=target, args=(*a, *extra)))
+        for p in procs:
+            p.start()
+        res = [q.get(timeout=timeout) for _ in procs]
+        for p in procs:
+            p.join(timeout=60)
+        return res
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu_band_rate(nodes, seed, procs, cols, reps, warm=0):
+    """Oracle band-LU solves/s of the workload on `procs` single-threaded host
+    processes, `cols` columns each: (rate, max seconds, solution of columns 0..cols-1)."""
+    res = _spawn_with_threads(1, _cpu_band_worker,
+                              [(nodes, seed, cols, i * cols, reps, warm) for i in range(procs)])
+    tmax = max(r[1] for r in res)
+    u0 = next(r[2] for r in res if r[0] == 0)
+    return procs * cols * max(reps, 1) / tmax, tmax, u0
+
+
+def cpu_baseline_leg(nodes, seed, cores, cols=4):
+    """The oracle on the host cores: the workload's band-LU solve on one core
+    and on every core (one process per core), and the dense FP64 apply of a
+    100 x 100 node grid (98^2 unknowns, inverse 0.74 GB) at B = 1 and 64 with
+    one BLAS thread and with all of them."""
+    t0 = time.perf_counter()
+    r1, t1, u0 = cpu_band_rate(nodes, seed, 1, cols, 1)
+    rall, tall, _ = cpu_band_rate(nodes, seed, cores, cols, 1)
+    d1 = _spawn_with_threads(1, _cpu_dense_worker, [(100, seed)])[0]
+    dall = _spawn_with_threads(cores, _cpu_dense_worker, [(100, seed)])[0]
+    return {
+        "value": rall, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": (f"numpy band-LU solve of {cols} of the {BATCH} columns per process, one "
+                   f"single-threaded process per host core ({cores}), started together "
+                   f"({tall:.2f} s); factorisation untimed (setup)"),
+        "host_cores": os.cpu_count(),
+        "single_core": {"value": r1, "unit": UNIT, "cores": 1,
+                        "sample": f"{cols} columns, one process ({t1:.2f} s)"},
+        "dense_apply_98sq": {
+            "unit": UNIT, "note": "oracle's dense FP64 inverse of a 100x100 node grid "
+                                  "(9604 unknowns) applied with numpy (BLAS); the 198^2 "
+                                  "inverse (12.3 GB) is not formed on the host",
+            "b1": {"single_thread": d1[1], "all_threads": dall[1]},
+            "b64": {"single_thread": d1[64], "all_threads": dall[64]},
+            "threads": cores},
+        "leg_seconds": time.perf_counter() - t0,
+    }, u0
 
 
 def reference_arm(args):
-    """--impl reference: the FP64 oracle, as it stands, on the host cores."""
+    """--impl reference: the FP64 oracle, as it stands, on the host cores (one
+    single-threaded band-LU process per core, each solving its own 4 columns of
+    the workload per step)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import numpy as np
-    from oracle import pide_oracle as O
-    from paper_1602_00001_gb300 import workloads as W
-    h = 1.0 / (NODES - 1)
-    eps = W.eps_fourier(NODES, NODES, h, seed=5)
     cols = 4
-    rho = W.moving_charges(NODES, NODES, h, seed=5, steps=cols)
-    b = O.rhs_from_charge(NODES, NODES, h, eps, rho)
-    fac = O.BandSolver(NODES, NODES, eps)
-    for _ in range(args.warmup):
-        fac.solve(b)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        fac.solve(b)
-    dt = (time.perf_counter() - t0) / max(args.steps, 1)
-    value = cols / dt
+    cores = max(1, min(os.cpu_count() or 1, BATCH // cols))
+    value, tmax, _ = cpu_band_rate(NODES, 5, cores, cols, args.steps, args.warmup)
+    dt = tmax / max(args.steps, 1)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": cols, "grid": "200x200",
-                   "sample": f"{cols} columns per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": {"workload": WORKLOAD, "global_batch": cols * cores, "grid": "200x200",
+                   "sample": f"{cols} columns per process per step, {cores} processes"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"numpy band-LU forward/back substitution, {cols} of the "
-                                   "1024 columns per step; factorisation untimed (setup)"},
+                                   f"1024 columns per process and step, {cores} single-threaded "
+                                   "processes started together; factorisation untimed (setup)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -501,9 +601,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default=None,
-                    choices=["bf16", "bf16_fp8", "fp16", "fp16_fp8", "fp8x2", "fp32"],
-                    help="stored format (default: fp16_fp8 for the 2-D apply and the adjoint, "
-                         "fp16 in 3-D)")
+                    choices=["auto", "bf16", "bf16_fp8", "fp16", "fp16_fp8", "fp8x2", "fp32"],
+                    help="stored format (default: auto -- chosen by the library from the measured "
+                         "contraction -- for the 2-D apply; fp16_fp8 for the adjoint, fp16 in 3-D)")
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--sweeps", type=int, default=-1, help="fixed sweep count (-1: calibrate)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
@@ -572,15 +672,29 @@ def main():
         torch.cuda.synchronize()
         return a.elapsed_time(z) / reps
 
-    fp64_b1_ms = timed(lambda: s64.apply(b[:1].contiguous()), 3)
+    fp64_b1_ms = timed(lambda: s64.apply(b[:1].contiguous()), 5)
     b64c = b[:64].contiguous()
-    fp64_b64_ms = timed(lambda: s64.apply(b64c), 1)
+    fp64_b64_ms = timed(lambda: s64.apply(b64c), 3)
+    # the whole batch through the FP64 apply (B = 1024: ~3 s per apply on the FP64 pipe)
+    fp64_bB_ms = None
+    if NN == NODES and B == BATCH:
+        u64_all = torch.empty_like(b)
+        fp64_bB_ms = timed(lambda: s64.apply(b, u64_all), 3)
+        del u64_all
     s64.close()
     del s64
     torch.cuda.empty_cache()
+    # FP64 peak of this GPU: cuBLAS DGEMM through torch (4096^3, best of 5)
+    Ad = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    fp64_gemm_ms = min(timed(lambda: torch.matmul(Ad, Ad), 1) for _ in range(5))
+    fp64_peak_tf = 2.0 * 4096 ** 3 / (fp64_gemm_ms * 1e-3) / 1e12
+    del Ad
+    torch.cuda.empty_cache()
 
-    # ---- the refined low-precision solver
+    # ---- the refined low-precision solver (the store chosen by the library unless forced)
     s = Solver(NN, NN, h, eps, args.precision)
+    auto_rep = s.auto_report() if args.precision == "auto" else None
+    args.precision = s.precision
     tune = dict(kv.split("=", 1) for kv in args.tune)
     if tune:
         s.set_tuning(**{k: int(v) for k, v in tune.items()})
@@ -619,6 +733,9 @@ def main():
             k1 = kk
             break
 
+    # the refinement's measured contraction on this batch (pide_info), outside the timed region
+    _, info_k = s.apply(b, u, sweeps=k, want_info=True)
+
     # ---- timed region: K steps of the whole refined batch
     for _ in range(args.warmup):
         s.apply(b, u, sweeps=k)
@@ -650,6 +767,7 @@ def main():
             s.apply(b1, u1, sweeps=k1)
     b1_apply_launches, b1_apply_ms = prof1["apply"]
     hi = s.info()
+    hi64_bytes = 8 * n * hi.ld
     sym_b1 = args.precision in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") and s.get_tuning()["symv"]
     b1_bytes = hi.store_bytes if not sym_b1 else \
         2 * 2 * (((n + 127) // 128) * (((n + 127) // 128) + 1) // 2) * 128 * 128
@@ -765,8 +883,25 @@ def main():
                             "avg_apply_ms": b1_apply_ms / max(b1_apply_launches, 1)}},
         "fp64_gpu": {"b1_solves_per_s": 1.0 / (fp64_b1_ms * 1e-3),
                      "b64_solves_per_s": 64.0 / (fp64_b64_ms * 1e-3),
-                     "speedup_b1024_vs_fp64": value / world / (64.0 / (fp64_b64_ms * 1e-3)),
-                     "speedup_b1_vs_fp64": fp64_b1_ms / b1_ms},
+                     "b1024_solves_per_s": (B / (fp64_bB_ms * 1e-3)) if fp64_bB_ms else None,
+                     "b1024_ms": fp64_bB_ms, "b1024_repeats": 3 if fp64_bB_ms else 0,
+                     "speedup_b1024_vs_fp64": (value / world / (B / (fp64_bB_ms * 1e-3)))
+                                              if fp64_bB_ms else None,
+                     "speedup_b1_vs_fp64": fp64_b1_ms / b1_ms,
+                     "fp64_peak_tflops": fp64_peak_tf,
+                     "fp64_peak_source": "cuBLAS DGEMM through torch.matmul, 4096^3, best of 5",
+                     "b1_fp64_tflops": 2.0 * n * n / (fp64_b1_ms * 1e-3) / 1e12,
+                     "b1024_fp64_tflops": (2.0 * n * n * B / (fp64_bB_ms * 1e-3) / 1e12)
+                                          if fp64_bB_ms else None,
+                     "b1_hbm_gbs": hi64_bytes / (fp64_b1_ms * 1e-3) / 1e9,
+                     "bound": "FP64 pipe: n^2 FP64 multiply-adds per column at B = 1 "
+                              "(the 12.3 GB inverse would stream in 1.8 ms at the HBM peak)"},
+        "contraction": {"measured": info_k.contraction, "sweeps": info_k.sweeps,
+                        "rel_residual": info_k.rel_residual, "apply_ms": info_k.ms,
+                        "source": "pide_info of one refined apply of the batch"},
+        "store": {"precision": args.precision,
+                  "chosen_by": "pide_setup_auto (measured contraction)" if auto_rep else "--precision",
+                  "auto": auto_rep},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": traffic,
                      "kernel": (f"gemm_tc2_kernel (tcgen05 cta_group::2 {args.precision}, M=256 N=256 per SM pair)"
@@ -789,16 +924,13 @@ def main():
                 "apply_host_one_batch_per_call": ah_value},
     }
     # ---- the oracle on the host cores (rank 0, N = 1 only), bounded sample
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and NN == NODES and B == BATCH:
         from oracle import pide_oracle as O
-        cols = 4
-        b_np = b[:cols].cpu().numpy()
-        rate, dt, fac, u_or = cpu_oracle_rate(NN, NN, h, eps, b_np, cols)
-        ur = u[:cols].cpu().numpy()
-        line["accuracy"]["max_rel_err_eq6_vs_oracle_2col"] = O.rel_error_eq6(ur[:2], u_or[:2])
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"numpy band-LU solve of {cols} of the {B} columns "
-                                          f"({dt:.1f} s); factorisation untimed (setup)"}
+        cores = max(1, min(os.cpu_count() or 1, BATCH // 4))
+        cpu_line, u_or = cpu_baseline_leg(NN, 5, cores, cols=4)
+        ur = u[:4].cpu().numpy()
+        line["accuracy"]["max_rel_err_eq6_vs_oracle_4col"] = O.rel_error_eq6(ur, u_or)
+        line["cpu_baseline"] = cpu_line
     line["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(line))

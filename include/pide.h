@@ -80,9 +80,17 @@ typedef enum {
                        below ~2^-115 loses bits to FP16 subnormals.  B = 1 uses the symmetric
                        two-term store as PIDE_BF16 does; not served by the batched entry
                        points */
-  PIDE_FP16_FP8 = 7 /* PIDE_FP16 plus the e4m3 correction term of PIDE_BF16_FP8, taken against
+  PIDE_FP16_FP8 = 7, /* PIDE_FP16 plus the e4m3 correction term of PIDE_BF16_FP8, taken against
                        the FP16 store; PIDE_TUNE_CORR_MASK defaults to 1 (the first apply) */
+  PIDE_AUTO = 8     /* setup only: the store is chosen by measurement, as pide_setup_auto does
+                       with its defaults (target 0.5e-6, 16 built-in probe right-hand sides,
+                       at most 8 sweeps); the handle then reports the chosen format */
 } pide_precision;
+
+/* max_sweeps value of pide_apply, pide_apply_host and pide_solve_stream that
+ * takes the sweep count measured for the handle by pide_setup_auto (EINVAL on
+ * a handle that was not set up that way). */
+#define PIDE_SWEEPS_AUTO (-1)
 
 typedef struct {
   int32_t nx;      /* nodes along x including the two boundary nodes, >= 3 */
@@ -101,7 +109,37 @@ typedef struct {
   int32_t converged;     /* 1 if tol was met (always 1 when tol <= 0) */
   double rel_residual;   /* max over columns of ||b - L u||_inf / ||b||_inf (FP64) */
   double setup_ms;       /* wall time of pide_setup for this handle */
+  double contraction;    /* measured per-sweep contraction of the refinement:
+                            (rel_residual / r_0)^(1/sweeps), r_0 = the same worst-column
+                            relative residual after the first apply, i.e. the geometric mean
+                            of ||r_k||_inf / ||r_k-1||_inf; NaN when no sweep ran */
+  double ms;             /* device time of the call's work (CUDA events on its stream), from
+                            the right-hand-side prep to the last apply; pide_apply_host
+                            includes its copies */
 } pide_info;
+
+/* One stored format measured by pide_setup_auto. */
+typedef struct {
+  int32_t precision;     /* pide_precision of the candidate store */
+  int32_t corr_mask;     /* applies that add its e4m3 correction term (0: none) */
+  int32_t sweeps;        /* fewest sweeps whose Eq. (6) error met the target on the probe;
+                            -1 if max_sweeps did not reach it */
+  double error;          /* Eq. (6) error on the probe after those sweeps (after max_sweeps
+                            when the target was missed), against the FP64 inverse */
+  double contraction;    /* geometric-mean error ratio per sweep (sweeps above 1e-12) */
+  double cost;           /* modelled cost of one refined apply in 16-bit GEMM units:
+                            (1 + sweeps) x (1, or 28 for FP32) + 0.5 per corrected apply
+                            + 0.15 per sweep (residual and prep) */
+} pide_auto_candidate;
+
+typedef struct {
+  double target;         /* Eq. (6) error the probe had to reach */
+  int32_t nprobe;        /* probe right-hand sides */
+  int32_t max_sweeps;
+  int32_t ncand;         /* entries of cand[] that were measured */
+  int32_t chosen;        /* index into cand[] of the store the handle keeps */
+  pide_auto_candidate cand[6];
+} pide_auto_report;
 
 typedef struct {
   int32_t n;             /* unknowns */
@@ -111,6 +149,8 @@ typedef struct {
   size_t store_bytes;    /* bytes of the stored inverse (+ scales) read per apply */
   double setup_ms;
   int32_t dims;          /* 2 (pide_setup) or 3 (pide_setup_3d) */
+  int32_t sweeps_hint;   /* sweeps measured by pide_setup_auto (what PIDE_SWEEPS_AUTO takes);
+                            -1 for handles set up with an explicit format or loaded */
 } pide_handle_info;
 
 /* Per-kernel-class event timing, recorded on the launching stream. */
@@ -162,6 +202,42 @@ pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precisio
  */
 pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host, pide_precision p,
                           void* stream, pide_handle* out);
+
+/*
+ * pide_setup_auto -- pide_setup with the stored format chosen by measurement.
+ * The paper rounds the inverse to k decimal digits and measures the error
+ * against the exact solution for each k (Table 1, and the numerical example's
+ * rounding of the inverse); here the candidate binary stores of the inverse are
+ * each measured by the error their refined apply reaches.  After step 2 the
+ * FP64 inverse G is held once; for each candidate -- FP16 + e4m3 correction in
+ * the first apply, FP16, BF16 + e4m3 correction in the first sweep, BF16, in
+ * that order, and FP32 only when none of them reaches the target -- the store
+ * is quantised from G, the probe right-hand sides are solved with
+ * k = 0, 1, ... max_sweeps refinement sweeps, and the Eq. (6) error against
+ * G's own FP64 apply is taken after each k.  The handle keeps the candidate
+ * of lowest modelled cost (pide_auto_candidate.cost) among those that reached
+ * the target (ties: the earlier one), with that sweep count as its
+ * sweeps_hint (pide_apply with max_sweeps = PIDE_SWEEPS_AUTO uses it).
+ *   target      Eq. (6) error to reach on the probe, in (0, 0.1].
+ *   probe_host  [nprobe][n] float64 right-hand sides on the HOST (Eq. 3 form),
+ *               or NULL for built-in probes: column j is b = -h^2 rho / d for a
+ *               charge rho of four Gaussian blobs (width 0.05, centres uniform in
+ *               [0.2, 0.8] along each axis, amplitudes uniform in [-1, 1]) drawn
+ *               from a counter-based generator (splitmix64) seeded by j.
+ *   nprobe      1 .. 256 probe columns.
+ *   max_sweeps  0 .. 30.
+ * The other arguments are pide_setup's.  Setup holds G and one candidate
+ * store at a time (12.3 GB + 4.6 GB at 198^2 unknowns) and takes a few
+ * milliseconds per probe solve beyond pide_setup.  pide_get_auto_report
+ * returns what was measured.  Errors: those of pide_setup; EINVAL for target,
+ * nprobe or max_sweeps out of range.
+ */
+pide_status pide_setup_auto(const pide_grid* g, const double* eps_host, double target,
+                            const double* probe_host, int32_t nprobe, int32_t max_sweeps,
+                            void* stream, pide_handle* out);
+
+/* The measurements behind a pide_setup_auto handle (EINVAL for other handles). */
+pide_status pide_get_auto_report(pide_handle h, pide_auto_report* out);
 
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void pide_destroy(pide_handle h);

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpide.so")
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8x2": 4, "bf16_fp8": 5, "fp16": 6,
-              "fp16_fp8": 7}
+              "fp16_fp8": 7, "auto": 8}
+SWEEPS_AUTO = -1          # PIDE_SWEEPS_AUTO: the sweep count pide_setup_auto measured
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
           6: "EUNSUPPORTED"}
 
@@ -32,13 +33,27 @@ class Grid3(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("contraction", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
 class HandleInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("ld", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("num_sms", ctypes.c_int32), ("store_bytes", ctypes.c_size_t),
-                ("setup_ms", ctypes.c_double), ("dims", ctypes.c_int32)]
+                ("setup_ms", ctypes.c_double), ("dims", ctypes.c_int32),
+                ("sweeps_hint", ctypes.c_int32)]
+
+
+class AutoCandidate(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("corr_mask", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("error", ctypes.c_double),
+                ("contraction", ctypes.c_double), ("cost", ctypes.c_double)]
+
+
+class AutoReport(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_double), ("nprobe", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("ncand", ctypes.c_int32),
+                ("chosen", ctypes.c_int32), ("cand", AutoCandidate * 6)]
 
 
 class Profile(ctypes.Structure):
@@ -59,6 +74,8 @@ _D = ctypes.c_double
 _SIGS = {
     "pide_setup": (_I, [ctypes.POINTER(Grid), _P, _I, _P, ctypes.POINTER(_P)]),
     "pide_setup_3d": (_I, [ctypes.POINTER(Grid3), _P, _I, _P, ctypes.POINTER(_P)]),
+    "pide_setup_auto": (_I, [ctypes.POINTER(Grid), _P, _D, _P, _I, _I, _P, ctypes.POINTER(_P)]),
+    "pide_get_auto_report": (_I, [_P, ctypes.POINTER(AutoReport)]),
     "pide_destroy": (None, [_P]),
     "pide_apply": (_I, [_P, _P, _P, _I, _I, _D, _P, _P, ctypes.POINTER(Info)]),
     "pide_apply_host": (_I, [_P, _P, _P, _I, _I, _D, _P, ctypes.POINTER(Info)]),
@@ -88,6 +105,9 @@ _SIGS = {
     "pide_last_error": (ctypes.c_char_p, []),
     "pide_version": (_I, []),
 }
+
+
+_PREC_NAMES = {v: k for k, v in PRECISIONS.items()}
 
 
 def load_library(path: str = LIB_PATH):
@@ -139,7 +159,10 @@ class Solver:
     'fp8' or 'fp8x2' (low-precision inverse, FP64 refinement), 'fp16' (FP16
     inverse and right-hand sides with power-of-two row / column scales), or
     'bf16_fp8' / 'fp16_fp8' (the BF16 / FP16 inverse plus an e4m3 correction
-    term added in the applies that the 'corr_mask' tuning key selects).
+    term added in the applies that the 'corr_mask' tuning key selects), or
+    'auto' (the store measured cheapest for a 0.5e-6 error: pide_setup with
+    PIDE_AUTO; ``Solver.auto`` sets the target and the probe).  ``precision``
+    then names the store the handle holds.
     """
 
     def __init__(self, nx: int, ny: int, h: float, eps=None, precision: str = "bf16",
@@ -165,6 +188,48 @@ class Solver:
                                        _stream(stream), ctypes.byref(h_out)), "pide_setup")
             self.handle = h_out
         self.eps = None if eps is None else np.asarray(eps, dtype=np.float64).reshape(self.ny, self.nx)
+        if self.precision == "auto":
+            self.precision = _PREC_NAMES[self.info().precision]
+
+    @classmethod
+    def auto(cls, nx: int, ny: int, h: float, eps=None, target: float = 0.5e-6, probe=None,
+             nprobe: int = 16, max_sweeps: int = 8, stream=None) -> "Solver":
+        """pide_setup_auto: the stored format chosen by the measured refinement
+        on ``probe`` ([nprobe][n] float64 right-hand sides on the host; None =
+        the library's built-in probes)."""
+        lib = load_library()
+        g = Grid(int(nx), int(ny), float(h))
+        eps_p, keep = None, None
+        if eps is not None:
+            keep = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(int(ny), int(nx)))
+            eps_p = keep.ctypes.data_as(ctypes.c_void_p)
+        probe_p = None
+        if probe is not None:
+            probe = np.ascontiguousarray(np.asarray(probe, dtype=np.float64)).reshape(
+                -1, (int(nx) - 2) * (int(ny) - 2))
+            nprobe = probe.shape[0]
+            probe_p = probe.ctypes.data_as(ctypes.c_void_p)
+        h_out = ctypes.c_void_p()
+        _check(lib.pide_setup_auto(ctypes.byref(g), eps_p, float(target), probe_p, int(nprobe),
+                                   int(max_sweeps), _stream(stream), ctypes.byref(h_out)),
+               "pide_setup_auto")
+        hi = HandleInfo()
+        _check(lib.pide_get_handle_info(h_out, ctypes.byref(hi)), "pide_get_handle_info")
+        obj = cls(nx, ny, h, None, _PREC_NAMES[hi.precision], _handle=h_out)
+        obj.eps = None if eps is None else keep
+        return obj
+
+    def auto_report(self) -> dict:
+        """What pide_setup_auto measured: target, probe size, and per candidate
+        store its sweeps to the target, error, contraction and modelled cost."""
+        r = AutoReport()
+        _check(self.lib.pide_get_auto_report(self.handle, ctypes.byref(r)), "pide_get_auto_report")
+        cands = [{"precision": _PREC_NAMES[c.precision], "corr_mask": c.corr_mask,
+                  "sweeps": c.sweeps, "error": c.error, "contraction": c.contraction,
+                  "cost": c.cost} for c in r.cand[:r.ncand]]
+        return {"target": r.target, "nprobe": r.nprobe, "max_sweeps": r.max_sweeps,
+                "chosen": cands[r.chosen]["precision"], "sweeps": cands[r.chosen]["sweeps"],
+                "candidates": cands}
 
     # -- life cycle
     def close(self):
@@ -401,6 +466,8 @@ class Solver3D(Solver):
                                       _stream(stream), ctypes.byref(h_out)), "pide_setup_3d")
         self.handle = h_out
         self.eps = None if eps is None else self._eps_keep
+        if self.precision == "auto":
+            self.precision = _PREC_NAMES[self.info().precision]
 
 
 def apply_batched(solvers, bs, us, sweeps: int = 2, stream=None):

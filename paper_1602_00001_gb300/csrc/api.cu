@@ -217,9 +217,11 @@ static pide_status solve_overlapped(pide_ctx* c, const double* b, int mode, cons
 // x = L^-1 D^-1 b = S^-1 b.  With an e4m3 correction term, apply k (0: the
 // first, k: sweep k) adds C e4m3(q(r)) when bit k of corr_mask is set.  FP16
 // right-hand sides take their power-of-two column scales once, from f, in the
-// prep; every residual of the solve reuses them.
-static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, double* x,
-                           int B, int sweeps, double tol, cudaStream_t st) {
+// prep; every residual of the solve reuses them.  hist (device, or NULL):
+// hist[k] = worst-column relative residual after apply k, recorded from the
+// refinement's own residuals (which are then tracked even without a tolerance).
+pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, double* x,
+                    int B, int sweeps, double tol, cudaStream_t st, double* hist) {
   PIDE_TRY(ensure_workspace(c, B));
   PIDE_CUDA_TRY(cudaMemsetAsync(c->flags, 0, FLAG_COUNT * sizeof(uint32_t), st));
   PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, 3 * (size_t)c->ws_B * sizeof(double), st));
@@ -229,8 +231,9 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
   // the e4m3 correction term joins the applies that corr_mask selects (tensor path)
   const bool corr = c->corr && tensor && (c->prec == PIDE_BF16 || c->prec == PIDE_FP16);
   auto corr_at = [&](int k) { return corr && k < 31 && ((c->corr_mask >> k) & 1); };
+  const bool track = tol > 0 || hist;
   if (c->overlap && tensor && tol <= 0 && sweeps > 0 && B >= 512 && c->aux && !corr &&
-      rf != RF_F16)
+      rf != RF_F16 && !hist)
     return solve_overlapped(c, b, mode, lift, x, B, sweeps, rf, st);
   // Low-precision stores take the double-float residual (its ~2^-45 |u|
   // rounding is far below their own error) unless the caller's tolerance
@@ -240,20 +243,21 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
                      c->prec == PIDE_FP16) &&
                     (tol <= 0 || tol >= 1e-8);
   if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
-  if (rf == RF_F16) PIDE_TRY(launch_prep_f16(c, b, B, mode, lift, tol > 0, st));
-  else PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, tol > 0, st, emul));
+  if (rf == RF_F16) PIDE_TRY(launch_prep_f16(c, b, B, mode, lift, track, st));
+  else PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, track, st, emul));
   if (corr_at(0)) PIDE_TRY(launch_corr_rhs(c, B, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
   if (corr_at(0)) PIDE_TRY(launch_apply_corr(c, B, x, st));
   for (int k = 0; k < sweeps; ++k) {
-    if (rf == RF_E4M3 && tol <= 0) {
+    if (rf == RF_E4M3 && tol <= 0 && !hist) {
       PIDE_TRY(launch_residual_fp8(c, b, x, B, mode, lift, st, emul));
       PIDE_TRY(launch_apply(c, B, x, true, st));
       continue;
     }
     if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, x, B, mode, lift, true, st));
-    PIDE_TRY(launch_residual(c, b, x, B, mode, lift, rf, true, nullptr, tol > 0, true, st, 0,
+    PIDE_TRY(launch_residual(c, b, x, B, mode, lift, rf, true, nullptr, track, true, st, 0,
                              emul));
+    if (hist && k < HIST_MAX) PIDE_TRY(launch_record(c, B, hist + k, tol <= 0, st));
     if (tol > 0) PIDE_TRY(launch_check(c, B, tol, st));
     if (corr_at(k + 1)) PIDE_TRY(launch_corr_rhs(c, B, st));
     PIDE_TRY(launch_apply(c, B, x, true, st));
@@ -264,7 +268,7 @@ static pide_status solve_s(pide_ctx* c, const double* b, int mode, const double*
 
 static pide_status fill_info(pide_ctx* c, const double* b, const double* x, int B, int mode,
                              const double* lift, int sweeps, double tol, cudaStream_t st,
-                             pide_info* info) {
+                             pide_info* info, bool timed = true) {
   // one more residual, tracked, ignoring the early-exit flag
   PIDE_CUDA_TRY(cudaMemsetAsync(c->colmax, 0, (size_t)c->ws_B * sizeof(double), st));
   if (tol <= 0) {
@@ -274,10 +278,15 @@ static pide_status fill_info(pide_ctx* c, const double* b, const double* x, int 
   PIDE_TRY(launch_residual(c, b, x, B, mode, lift, RF_F64, false, nullptr, true, false, st));
   std::vector<double> cm(2 * (size_t)c->ws_B);
   uint32_t fl[FLAG_COUNT];
+  double r0 = 0.0;
   PIDE_CUDA_TRY(cudaMemcpyAsync(cm.data(), c->colmax, cm.size() * sizeof(double),
                                 cudaMemcpyDeviceToHost, st));
   PIDE_CUDA_TRY(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+  PIDE_CUDA_TRY(cudaMemcpyAsync(&r0, c->hist, sizeof(double), cudaMemcpyDeviceToHost, st));
   PIDE_CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.0f;
+  if (timed && cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]) != cudaSuccess) ms = 0.0f;
+  info->ms = ms;
   double worst = 0.0;
   for (int k = 0; k < B; ++k) {
     const double den = cm[c->ws_B + k];
@@ -293,6 +302,10 @@ static pide_status fill_info(pide_ctx* c, const double* b, const double* x, int 
     info->converged = 1;
     info->sweeps = sweeps;
   }
+  // geometric mean of the per-sweep residual ratios: (r_K / r_0)^(1/K)
+  info->contraction = std::nan("");
+  if (info->sweeps > 0 && r0 > 0.0)
+    info->contraction = std::pow(worst / r0, 1.0 / info->sweeps);
   if (fl[FLAG_ERROR]) {
     set_error("device-side wait timed out (code " + std::to_string(fl[FLAG_ERROR]) + ")");
     return PIDE_ETIMEOUT;
@@ -366,6 +379,9 @@ static pide_status setup_operator(pide_ctx* c, int nx, int ny, int nz, double h,
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->w, faces * (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->lift, (size_t)c->n * sizeof(double)));
   PIDE_CUDA_TRY(cudaMalloc((void**)&c->flags, FLAG_COUNT * sizeof(uint32_t)));
+  PIDE_CUDA_TRY(cudaMalloc((void**)&c->hist, HIST_MAX * sizeof(double)));
+  PIDE_CUDA_TRY(cudaMemset(c->hist, 0, HIST_MAX * sizeof(double)));
+  for (int k = 0; k < 2; ++k) PIDE_CUDA_TRY(cudaEventCreate(&c->tev[k]));
 
   PIDE_CUDA_TRY(cudaMemset(c->flags, 0, FLAG_COUNT * sizeof(uint32_t)));
   int prio_lo = 0, prio_hi = 0;
@@ -384,10 +400,20 @@ static pide_status setup_operator(pide_ctx* c, int nx, int ny, int nz, double h,
   return PIDE_OK;
 }
 
+// Arguments of the measured format choice (pide_setup_auto / PIDE_AUTO).
+struct AutoArgs {
+  double target = 0.5e-6;
+  const double* probe_host = nullptr;
+  int nprobe = 16;
+  int max_sweeps = 8;
+};
+
 // Steps 1-2 for a 2-D (dims 2) or 3-D (dims 3) grid: assemble, invert in FP64,
-// quantise; the handle is returned only when every step succeeded.
+// quantise (PIDE_AUTO: the store the measurement chooses); the handle is
+// returned only when every step succeeded.
 static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, const double* eps_host,
-                                pide_precision p, void* stream, pide_handle* out) {
+                                pide_precision p, void* stream, pide_handle* out,
+                                const AutoArgs& aa = AutoArgs()) {
   if (eps_host) {
     const size_t N = (size_t)nx * ny * (dims == 3 ? nz : 1);
     for (size_t k = 0; k < N; ++k)
@@ -408,6 +434,8 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
   pide_ctx* c = new pide_ctx();
   // the BF16 / FP16 store plus its e4m3 correction term
   const bool want_corr = p == PIDE_BF16_FP8 || p == PIDE_FP16_FP8;
+  const bool want_auto = p == PIDE_AUTO;
+  if (want_auto) p = PIDE_FP64;                 // until the measurement has chosen
   if (p == PIDE_BF16_FP8) p = PIDE_BF16;
   if (p == PIDE_FP16_FP8) {
     p = PIDE_FP16;
@@ -428,13 +456,18 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
     }
   }
   if (s == PIDE_OK) s = build_inverse_fp64(c, G, st);
+  if (s == PIDE_OK && want_auto) {
+    // leaves the chosen store quantised in the handle
+    s = auto_select(c, G, aa.target, aa.probe_host, aa.nprobe, aa.max_sweeps, st);
+    p = c->prec;
+  }
   if (s == PIDE_OK) {
     if (p == PIDE_FP64) {
       c->inv = G;
       c->store_bytes = (size_t)c->n * c->ld * sizeof(double);
       G = nullptr;
     } else {
-      s = quantize_store(c, G, st);
+      if (!want_auto) s = quantize_store(c, G, st);
       if (s == PIDE_OK && want_corr) s = quantize_corr(c, G, st);
       // B = 1 of both 16-bit stores: the symmetric two-term BF16 form of S^-1
       if (s == PIDE_OK && (p == PIDE_BF16 || p == PIDE_FP16)) s = build_sym_store(c, G, st);
@@ -462,11 +495,38 @@ static pide_status setup_handle(int nx, int ny, int nz, double h, int dims, cons
 extern "C" pide_status pide_setup(const pide_grid* g, const double* eps_host, pide_precision p,
                                   void* stream, pide_handle* out) {
   if (out) *out = nullptr;
-  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 7) {
+  if (!out || !valid_grid(g) || (int)p < 0 || (int)p > 8) {
     set_error("pide_setup: bad argument");
     return PIDE_EINVAL;
   }
   return setup_handle(g->nx, g->ny, 1, g->h, 2, eps_host, p, stream, out);
+}
+
+extern "C" pide_status pide_setup_auto(const pide_grid* g, const double* eps_host, double target,
+                                       const double* probe_host, int32_t nprobe,
+                                       int32_t max_sweeps, void* stream, pide_handle* out) {
+  if (out) *out = nullptr;
+  if (!out || !valid_grid(g) || !(target > 0.0 && target <= 0.1) || nprobe < 1 || nprobe > 256 ||
+      max_sweeps < 0 || max_sweeps > 30) {
+    set_error("pide_setup_auto: bad argument (grid, target in (0, 0.1], nprobe in [1, 256], "
+              "max_sweeps in [0, 30])");
+    return PIDE_EINVAL;
+  }
+  AutoArgs aa;
+  aa.target = target;
+  aa.probe_host = probe_host;
+  aa.nprobe = nprobe;
+  aa.max_sweeps = max_sweeps;
+  return setup_handle(g->nx, g->ny, 1, g->h, 2, eps_host, PIDE_AUTO, stream, out, aa);
+}
+
+extern "C" pide_status pide_get_auto_report(pide_handle h, pide_auto_report* out) {
+  if (!h || !out || !h->has_auto) {
+    set_error("pide_get_auto_report: bad argument (handle from pide_setup_auto, out)");
+    return PIDE_EINVAL;
+  }
+  *out = h->auto_rep;
+  return PIDE_OK;
 }
 
 extern "C" pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host,
@@ -474,7 +534,7 @@ extern "C" pide_status pide_setup_3d(const pide_grid3* g, const double* eps_host
   if (out) *out = nullptr;
   const bool ok = g && g->nx >= 3 && g->ny >= 3 && g->nz >= 3 && std::isfinite(g->h) && g->h > 0 &&
                   (int64_t)(g->nx - 2) * (g->ny - 2) * (g->nz - 2) < (int64_t)1 << 30;
-  if (!out || !ok || (int)p < 0 || (int)p > 7) {
+  if (!out || !ok || (int)p < 0 || (int)p > 8) {
     set_error("pide_setup_3d: bad argument");
     return PIDE_EINVAL;
   }
@@ -487,7 +547,7 @@ extern "C" void pide_destroy(pide_handle h) {
   cudaDeviceSynchronize();
   void* ptrs[] = {h->sym, h->sym_lo, h->sym_scale, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
                   h->corr, h->corr_scale, h->Rc, h->col_scale_c,
-                  h->lift, h->colmax, h->flags, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
+                  h->lift, h->colmax, h->flags, h->hist, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : h->prof_events) {
@@ -499,6 +559,8 @@ extern "C" void pide_destroy(pide_handle h) {
   for (cudaEvent_t e : h->hev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->sev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->tev)
     if (e) cudaEventDestroy(e);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->cstream) cudaStreamDestroy(h->cstream);
@@ -517,29 +579,47 @@ static pide_status check_apply_args(pide_handle h, const void* b, const void* u,
   return PIDE_OK;
 }
 
+// PIDE_SWEEPS_AUTO -> the sweep count pide_setup_auto measured for the handle.
+static pide_status resolve_sweeps(pide_handle h, int32_t* sweeps) {
+  if (h && *sweeps == PIDE_SWEEPS_AUTO) {
+    if (h->sweeps_hint < 0) {
+      set_error("PIDE_SWEEPS_AUTO needs a handle from pide_setup_auto");
+      return PIDE_EINVAL;
+    }
+    *sweeps = h->sweeps_hint;
+  }
+  return PIDE_OK;
+}
+
 extern "C" pide_status pide_apply(pide_handle h, const double* b_dev, double* u_dev, int32_t B,
                                   int32_t max_sweeps, double tol, const double* g_dev,
                                   void* stream, pide_info* info) {
+  PIDE_TRY(resolve_sweeps(h, &max_sweeps));
   PIDE_TRY(check_apply_args(h, b_dev, u_dev, B, max_sweeps));
   if (B == 0) {
-    if (info) *info = pide_info{0, 1, 0.0, h->setup_ms};
+    if (info) *info = pide_info{0, 1, 0.0, h->setup_ms, std::nan(""), 0.0};
     return PIDE_OK;
   }
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
+  if (info) PIDE_CUDA_TRY(cudaEventRecord(h->tev[0], st));
   const double* lift = nullptr;
   if (g_dev) {
     PIDE_TRY(launch_lift(h, g_dev, st));
     lift = h->lift;
   }
-  PIDE_TRY(solve_s(h, b_dev, 0, lift, u_dev, B, max_sweeps, tol, st));
-  if (info) return fill_info(h, b_dev, u_dev, B, 0, lift, max_sweeps, tol, st, info);
+  PIDE_TRY(solve_s(h, b_dev, 0, lift, u_dev, B, max_sweeps, tol, st, info ? h->hist : nullptr));
+  if (info) {
+    PIDE_CUDA_TRY(cudaEventRecord(h->tev[1], st));
+    return fill_info(h, b_dev, u_dev, B, 0, lift, max_sweeps, tol, st, info);
+  }
   return PIDE_OK;
 }
 
 extern "C" pide_status pide_apply_host(pide_handle h, const double* b_host, double* u_host,
                                        int32_t B, int32_t max_sweeps, double tol, void* stream,
                                        pide_info* info) {
+  PIDE_TRY(resolve_sweeps(h, &max_sweeps));
   PIDE_TRY(check_apply_args(h, b_host, u_host, B, max_sweeps));
   if (B == 0) return PIDE_OK;
   PIDE_CUDA_TRY(cudaSetDevice(h->device));
@@ -582,10 +662,15 @@ extern "C" pide_status pide_apply_host(pide_handle h, const double* b_host, doub
     PIDE_CUDA_TRY(cudaStreamWaitEvent(st, out, 0));
     return check_device_error(h, st);
   }
+  if (info) PIDE_CUDA_TRY(cudaEventRecord(h->tev[0], st));
   PIDE_CUDA_TRY(cudaMemcpyAsync(h->hbuf_b, b_host, bytes, cudaMemcpyHostToDevice, st));
-  PIDE_TRY(solve_s(h, h->hbuf_b, 0, nullptr, h->hbuf_u, B, max_sweeps, tol, st));
+  PIDE_TRY(solve_s(h, h->hbuf_b, 0, nullptr, h->hbuf_u, B, max_sweeps, tol, st,
+                   info ? h->hist : nullptr));
   PIDE_CUDA_TRY(cudaMemcpyAsync(u_host, h->hbuf_u, bytes, cudaMemcpyDeviceToHost, st));
-  if (info) return fill_info(h, h->hbuf_b, h->hbuf_u, B, 0, nullptr, max_sweeps, tol, st, info);
+  if (info) {
+    PIDE_CUDA_TRY(cudaEventRecord(h->tev[1], st));
+    return fill_info(h, h->hbuf_b, h->hbuf_u, B, 0, nullptr, max_sweeps, tol, st, info);
+  }
   return check_device_error(h, st);
 }
 
@@ -598,6 +683,7 @@ extern "C" pide_status pide_apply_host(pide_handle h, const double* b_host, doub
 extern "C" pide_status pide_solve_stream(pide_handle h, const double* in_host, double* u_host,
                                          int64_t T, int32_t chunk, int32_t sweeps,
                                          int32_t charge, void* stream) {
+  PIDE_TRY(resolve_sweeps(h, &sweeps));
   if (!h || T < 0 || chunk < 1 || chunk > 65535 || sweeps < 0 || (T > 0 && (!in_host || !u_host)) ||
       (const void*)in_host == (const void*)u_host) {
     set_error("pide_solve_stream: bad argument (handle, pointers, T >= 0, chunk in [1, 65535], "
@@ -929,6 +1015,7 @@ extern "C" pide_status pide_get_handle_info(pide_handle h, pide_handle_info* out
   out->store_bytes = h->store_bytes;
   out->setup_ms = h->setup_ms;
   out->dims = h->dims;
+  out->sweeps_hint = h->sweeps_hint;
   return PIDE_OK;
 }
 

@@ -130,6 +130,14 @@ struct pide_ctx {
   int resid_emul = 1;               // refinement residual in double-float (off the FP64 pipe)
   int resid_shape = -1;             // its launch shape: -1 default (8 nodes per thread); 0..3: 4, 8, 2, 16
   int resid_prefetch = 4;           // its L2 prefetch distance in column pairs (0: none)
+  // refinement history of a pide_apply that fills pide_info: the worst-column
+  // relative residual after apply k (k < HIST_MAX), and events timing the call
+  double* hist = nullptr;
+  cudaEvent_t tev[2] = {nullptr, nullptr};
+  // pide_setup_auto: what was measured, and the sweep count it chose
+  bool has_auto = false;
+  pide_auto_report auto_rep = {};
+  int sweeps_hint = -1;
   // profiling
   bool prof_on = false;
   struct Ev { cudaEvent_t a, b; int cls; };
@@ -164,6 +172,21 @@ pide_status launch_residual(pide_ctx* c, const double* b, const double* u, int B
                             const double* lift, int rfmt, bool write_R, double* r_out, bool track,
                             bool honor_done, cudaStream_t st, int col0 = 0, bool emul = false);
 pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
+// *slot = max over columns of colmax[c] / max|f_c| (the residual just tracked);
+// reset: zero colmax afterwards (the tolerance check does it when tol > 0).
+// Skipped once the tolerance flag marks the solve done.
+pide_status launch_record(pide_ctx* c, int B, double* slot, bool reset, cudaStream_t st);
+constexpr int HIST_MAX = 64;
+// The refined solve of step 3 (api.cu): x = Q(L^-1) q(f), then `sweeps` sweeps
+// x += Q(L^-1) q(f - L x); hist (device, may be NULL): per-sweep residual record.
+pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, double* x,
+                    int B, int sweeps, double tol, cudaStream_t st, double* hist = nullptr);
+// The workspace sized for another right-hand-side format is released (select.cu).
+void drop_workspace(pide_ctx* c);
+// PIDE_AUTO (select.cu): measure the candidate stores against G = L^-1 (FP64) and
+// leave the chosen one quantised in the handle (prec, corr, corr_mask, sweeps_hint).
+pide_status auto_select(pide_ctx* c, const double* G, double target, const double* probe_host,
+                        int nprobe, int max_sweeps, cudaStream_t st);
 // FP8 right-hand sides in one FP64 pass: residual to FP32 scratch with the column
 // maxima, per-column scale, then e4m3 quantisation of the scratch into R.
 pide_status launch_residual_fp8(pide_ctx* c, const double* b, const double* u, int B, int mode,

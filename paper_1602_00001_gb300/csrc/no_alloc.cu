@@ -15,13 +15,21 @@
 // loads the library holds that array until the process exits.
 //
 // The scratch array is shared by every call in the process: each call
-// overwrites what it needs before reading it (nothing in it has to start at
-// zero), and two calls whose work overlaps on the GPU (different streams, or
-// different threads) race on it -- serialise them.
+// rewrites all of it that it reads (the right-hand side and its zero padding)
+// before reading it, so nothing has to start at zero, and two calls whose work
+// overlaps on the GPU (different streams, or different threads) race on it --
+// serialise them.
 //
-// The product here is a plain warp-per-row matrix-vector kernel reading the
-// right-hand side from the scratch array; the numbers match pide_apply up to
-// FP32 summation order.
+// What it computes: the same refinement as pide_apply (first apply, then
+// `sweeps` times an FP64 stencil residual and an apply-accumulate), with every
+// right-hand side handed to the stored inverse in FP32 (pide_apply hands the
+// tensor cores FP16, BF16 or e4m3).  The e4m3 correction term of a *_FP8 store
+// joins the applies its correction mask selects, as in pide_apply.  So the two
+// entry points agree once the refinement has converged, not apply by apply;
+// an FP64 store needs two sweeps to come back from the FP32 right-hand side to
+// FP64 accuracy.  The product is a CUDA-core matrix-vector kernel: FP32
+// accumulation (FP64 for the FP64 store), 16-byte loads of the stored rows,
+// four rows per warp sharing each load of the right-hand side.
 #include <mutex>
 
 #include "common.cuh"
@@ -33,7 +41,8 @@ constexpr int NOALLOC_MAX_COLS = 8;
 constexpr int NOALLOC_MAX_N = 65536;
 constexpr size_t NOALLOC_SCRATCH_FLOATS = (size_t)NOALLOC_MAX_COLS * NOALLOC_MAX_N;
 
-// File-scope scratch: [NOALLOC_MAX_COLS][n] FP32 right-hand side / residual.
+// File-scope scratch: [NOALLOC_MAX_COLS][ldr] FP32 right-hand side / residual,
+// ldr = n rounded up to 16 (<= NOALLOC_MAX_N), zero past n.
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
 
 // Host code cannot use g_noalloc_scratch as a device address; its address on
@@ -63,76 +72,250 @@ pide_status noalloc_scratch(int dev, float** out) {
   return PIDE_OK;
 }
 
-// R[col][p] = float(b) (first apply) or float(b - L u) (FP64 residual of Eq. 3).
+// R[col][p] = float(b) (first apply) or float(b - L u) (FP64 residual of Eq. 3)
+// for p < n, and 0 for n <= p < ldr.
 __global__ void noalloc_rhs_kernel(const double* __restrict__ b, const double* __restrict__ u,
-                                   const double* __restrict__ w4, int n, int mx, int residual,
-                                   float* __restrict__ R) {
+                                   const double* __restrict__ w4, int n, int ldr, int mx,
+                                   int residual, float* __restrict__ R) {
   const int col = blockIdx.y;
   const double* bc = b + (size_t)col * n;
   const double* uc = u + (size_t)col * n;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    double r = bc[p];
-    if (residual) {
-      const int c = p % mx;
-      r -= uc[p];
-      if (c > 0) r = fma(w4[p], uc[p - 1], r);
-      if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
-      if (p >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
-      if (p + mx < n) r = fma(w4[3 * n + p], uc[p + mx], r);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ldr; p += gridDim.x * blockDim.x) {
+    double r = 0.0;
+    if (p < n) {
+      r = bc[p];
+      if (residual) {
+        const int c = p % mx;
+        r -= uc[p];
+        if (c > 0) r = fma(w4[p], uc[p - 1], r);
+        if (c < mx - 1) r = fma(w4[n + p], uc[p + 1], r);
+        if (p >= mx) r = fma(w4[2 * n + p], uc[p - mx], r);
+        if (p + mx < n) r = fma(w4[3 * n + p], uc[p + mx], r);
+      }
     }
-    R[(size_t)col * n + p] = (float)r;
+    R[(size_t)col * ldr + p] = (float)r;
   }
 }
 
-__device__ __forceinline__ float stored_entry(const void* inv, const void* inv_lo, int fmt,
-                                              size_t e) {
-  switch (fmt) {
-    case PIDE_FP64: return (float)reinterpret_cast<const double*>(inv)[e];
-    case PIDE_FP32: return reinterpret_cast<const float*>(inv)[e];
-    case PIDE_BF16: return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(inv)[e]);
-    case PIDE_FP16: return __half2float(reinterpret_cast<const __half*>(inv)[e]);   // row scale outside
-    default: {
-      float v = (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv)[e];
-      if (inv_lo) v += (float)reinterpret_cast<const __nv_fp8_e4m3*>(inv_lo)[e];
-      return v;
+// Stored entries per 16-byte load, and their conversion to FP32.
+template <int KIND> struct Store;
+template <> struct Store<KIND_F64> { static constexpr int V = 2; };
+template <> struct Store<KIND_F32> { static constexpr int V = 4; };
+template <> struct Store<KIND_BF16> { static constexpr int V = 8; };
+template <> struct Store<KIND_F16> { static constexpr int V = 8; };
+template <> struct Store<KIND_FP8> { static constexpr int V = 16; };
+
+__device__ __forceinline__ float e4m3_value(uint32_t byte) {
+  __nv_fp8_e4m3 v;
+  v.__x = (uint8_t)byte;
+  return (float)v;
+}
+
+template <int KIND>
+__device__ __forceinline__ void to_float(const uint4& raw, float (&a)[Store<KIND>::V]) {
+  const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+  if constexpr (KIND == KIND_F32) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = __uint_as_float(w[i]);
+  } else if constexpr (KIND == KIND_BF16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[2 * i] = __uint_as_float(w[i] << 16);
+      a[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
     }
+  } else if constexpr (KIND == KIND_F16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+      a[2 * i] = f.x;
+      a[2 * i + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[4 * i + k] = e4m3_value(w[i] >> (8 * k));
   }
 }
 
-// One warp per row p: u[col][p] (=|+=) scale_p * sum_q Q[p][q] R[col][q].
-// The FP64 store is read in FP64 and summed in FP64.
+// The second term of a row, V e4m3 entries at the same positions: the FP8X2
+// lo term (same row scale) or the e4m3 correction term (its own row scale).
+template <int V>
+__device__ __forceinline__ void second_term(const uint8_t* p, float (&a)[V]) {
+  if constexpr (V == 16) {
+    const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[4 * i + k] = e4m3_value(w[i] >> (8 * k));
+  } else if constexpr (V == 8) {
+    const uint2 raw = __ldcs(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = e4m3_value(raw.x >> (8 * k));
+      a[4 + k] = e4m3_value(raw.y >> (8 * k));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) a[k] = e4m3_value(p[k]);
+  }
+}
+
+// u[c][p] (=|+=) scale_p * sum_q A[p][q] R[c][q] for the ROWS rows of each warp.
+// A[p][q] = Q + ratio_p * T (T: the FP8X2 lo term with ratio 1, or the
+// correction term C with ratio c_p / s_p), accumulated in FP32 and scaled by
+// s_p (the row scale, 1 for BF16 and FP32) in FP64 at the end.
+template <int KIND, int ROWS>
 __global__ void __launch_bounds__(256) noalloc_gemv_kernel(
-    const void* __restrict__ inv, const void* __restrict__ inv_lo,
-    const float* __restrict__ row_scale, int fmt, int ld, int n, int B,
-    const float* __restrict__ R, double* __restrict__ u, int accumulate) {
+    const void* __restrict__ inv, const uint8_t* __restrict__ second,
+    const float* __restrict__ row_scale, const float* __restrict__ second_scale, int ld, int n,
+    int ldr, int B, const float* __restrict__ R, double* __restrict__ u, int accumulate) {
+  constexpr int V = Store<KIND>::V;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int p0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ROWS; p0 < n; p0 += warps * ROWS) {
+    float acc[ROWS][NOALLOC_MAX_COLS];
+    float ratio[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+      for (int c = 0; c < NOALLOC_MAX_COLS; ++c) acc[r][c] = 0.0f;
+      const int p = min(p0 + r, n - 1);
+      const float s = row_scale ? row_scale[p] : 1.0f;
+      ratio[r] = second ? (second_scale ? second_scale[p] / s : 1.0f) : 0.0f;
+    }
+    for (int q = lane * V; q < ldr; q += 32 * V) {
+      float a[ROWS][V];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const int p = min(p0 + r, n - 1);
+        const size_t e = (size_t)p * ld + q;
+        const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(
+            reinterpret_cast<const uint8_t*>(inv) + e * (16 / V)));
+        to_float<KIND>(raw, a[r]);
+        if (second) {
+          float t[V];
+          second_term<V>(second + e, t);
+#pragma unroll
+          for (int v = 0; v < V; ++v) a[r][v] = fmaf(ratio[r], t[v], a[r][v]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NOALLOC_MAX_COLS; ++c) {
+        if (c >= B) break;
+        const float4* x4 = reinterpret_cast<const float4*>(R + (size_t)c * ldr + q);
+#pragma unroll
+        for (int v4 = 0; v4 < V / 4; ++v4) {
+          const float4 x = __ldg(x4 + v4);
+#pragma unroll
+          for (int r = 0; r < ROWS; ++r) {
+            acc[r][c] = fmaf(a[r][4 * v4 + 0], x.x, acc[r][c]);
+            acc[r][c] = fmaf(a[r][4 * v4 + 1], x.y, acc[r][c]);
+            acc[r][c] = fmaf(a[r][4 * v4 + 2], x.z, acc[r][c]);
+            acc[r][c] = fmaf(a[r][4 * v4 + 3], x.w, acc[r][c]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int c = 0; c < NOALLOC_MAX_COLS; ++c)
+        for (int o = 16; o > 0; o >>= 1) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], o);
+    // lane r * 8 + c writes row p0 + r, column c
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int c = 0; c < NOALLOC_MAX_COLS; ++c)
+        if (lane == r * NOALLOC_MAX_COLS + c && c < B && p0 + r < n) {
+          const int p = p0 + r;
+          const double s = row_scale ? (double)row_scale[p] : 1.0;
+          double* dst = u + (size_t)c * n + p;
+          const double v = (double)acc[r][c] * s;
+          *dst = accumulate ? *dst + v : v;
+        }
+  }
+}
+
+// The FP64 store: one warp per row, FP64 products and sums.
+__global__ void __launch_bounds__(256) noalloc_gemv_f64_kernel(
+    const double* __restrict__ inv, int ld, int n, int ldr, int B, const float* __restrict__ R,
+    double* __restrict__ u, int accumulate) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += warps) {
     double acc[NOALLOC_MAX_COLS];
 #pragma unroll
     for (int c = 0; c < NOALLOC_MAX_COLS; ++c) acc[c] = 0.0;
-    const size_t row = (size_t)p * ld;
-    for (int q = lane; q < n; q += 32) {
-      const double a = fmt == PIDE_FP64 ? reinterpret_cast<const double*>(inv)[row + q]
-                                        : (double)stored_entry(inv, inv_lo, fmt, row + q);
+    const double* row = inv + (size_t)p * ld;
+    for (int q = lane * 2; q < ldr; q += 64) {
+      const double2 a = __ldcs(reinterpret_cast<const double2*>(row + q));
 #pragma unroll
-      for (int c = 0; c < NOALLOC_MAX_COLS; ++c)
-        if (c < B) acc[c] = fma(a, (double)R[(size_t)c * n + q], acc[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < NOALLOC_MAX_COLS; ++c) {
-      double v = acc[c];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[c] = v;
-    }
-    if (lane == 0) {
-      const double s = row_scale ? (double)row_scale[p] : 1.0;
-      for (int c = 0; c < B; ++c) {
-        double* dst = u + (size_t)c * n + p;
-        *dst = accumulate ? *dst + acc[c] * s : acc[c] * s;
+      for (int c = 0; c < NOALLOC_MAX_COLS; ++c) {
+        if (c >= B) break;
+        const float2 x = __ldg(reinterpret_cast<const float2*>(R + (size_t)c * ldr + q));
+        acc[c] = fma(a.x, (double)x.x, acc[c]);
+        acc[c] = fma(a.y, (double)x.y, acc[c]);
       }
     }
+#pragma unroll
+    for (int c = 0; c < NOALLOC_MAX_COLS; ++c)
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+#pragma unroll
+    for (int c = 0; c < NOALLOC_MAX_COLS; ++c)
+      if (lane == c && c < B) {
+        double* dst = u + (size_t)c * n + p;
+        *dst = accumulate ? *dst + acc[c] : acc[c];
+      }
   }
+}
+
+pide_status launch_noalloc_gemv(pide_ctx* c, const float* R, int ldr, int B, double* u,
+                                bool accumulate, bool corrected, cudaStream_t st) {
+  const int acc = accumulate ? 1 : 0;
+  const int threads = 256;
+  if (c->prec == PIDE_FP64) {
+    int grid = (c->n + 7) / 8;
+    if (grid > c->num_sms * 16) grid = c->num_sms * 16;
+    noalloc_gemv_f64_kernel<<<grid, threads, 0, st>>>((const double*)c->inv, c->ld, c->n, ldr, B,
+                                                      R, u, acc);
+    return PIDE_OK;
+  }
+  // the second term: the FP8X2 lo term, or the correction term in the applies that add it
+  const uint8_t* second = nullptr;
+  const float* second_scale = nullptr;
+  if (c->prec == PIDE_FP8X2) {
+    second = (const uint8_t*)c->inv_lo;
+  } else if (corrected && c->corr) {
+    second = (const uint8_t*)c->corr;
+    second_scale = c->corr_scale;
+  }
+  const float* rs = (c->prec == PIDE_FP16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2)
+                        ? c->row_scale : nullptr;
+  auto grid_for = [&](int rows) {
+    int g = (c->n + rows * 8 - 1) / (rows * 8);
+    return g > c->num_sms * 16 ? c->num_sms * 16 : g;
+  };
+  switch (c->prec) {
+    case PIDE_FP32:
+      noalloc_gemv_kernel<KIND_F32, 4><<<grid_for(4), threads, 0, st>>>(
+          c->inv, second, rs, second_scale, c->ld, c->n, ldr, B, R, u, acc);
+      break;
+    case PIDE_BF16:
+      noalloc_gemv_kernel<KIND_BF16, 4><<<grid_for(4), threads, 0, st>>>(
+          c->inv, second, rs, second_scale, c->ld, c->n, ldr, B, R, u, acc);
+      break;
+    case PIDE_FP16:
+      noalloc_gemv_kernel<KIND_F16, 4><<<grid_for(4), threads, 0, st>>>(
+          c->inv, second, rs, second_scale, c->ld, c->n, ldr, B, R, u, acc);
+      break;
+    default:   // PIDE_FP8, PIDE_FP8X2 (e4m3 hi (+ lo) with the row scale)
+      noalloc_gemv_kernel<KIND_FP8, 2><<<grid_for(2), threads, 0, st>>>(
+          c->inv, second, rs, second_scale, c->ld, c->n, ldr, B, R, u, acc);
+      break;
+  }
+  return PIDE_OK;
 }
 
 }  // namespace
@@ -162,19 +345,20 @@ extern "C" pide_status pide_apply_noalloc(pide_handle h, const double* b_dev, do
   float* R = nullptr;
   PIDE_TRY(noalloc_scratch(h->device, &R));
   cudaStream_t st = (cudaStream_t)stream;
-  const dim3 rgrid((h->n + 255) / 256, B);
-  const int ggrid = h->num_sms * 8;
-  const int fmt = (int)h->prec;
-  noalloc_rhs_kernel<<<rgrid, 256, 0, st>>>(b_dev, u_dev, h->w, h->n, h->mx, 0, R);
+  const int ldr = (h->n + 15) / 16 * 16;           // <= NOALLOC_MAX_N and <= h->ld
+  int gx = (ldr + 255) / 256;
+  if (gx > 1024) gx = 1024;
+  const dim3 rgrid(gx, B);
+  // apply k adds the e4m3 correction term when bit k of the handle's mask is set
+  auto corrected = [&](int k) { return h->corr && k < 31 && ((h->corr_mask >> k) & 1); };
+  noalloc_rhs_kernel<<<rgrid, 256, 0, st>>>(b_dev, u_dev, h->w, h->n, ldr, h->mx, 0, R);
   PIDE_CUDA_TRY(cudaGetLastError());
-  noalloc_gemv_kernel<<<ggrid, 256, 0, st>>>(h->inv, h->inv_lo, h->row_scale, fmt, h->ld, h->n,
-                                             B, R, u_dev, 0);
+  PIDE_TRY(launch_noalloc_gemv(h, R, ldr, B, u_dev, false, corrected(0), st));
   PIDE_CUDA_TRY(cudaGetLastError());
   for (int k = 0; k < sweeps; ++k) {
-    noalloc_rhs_kernel<<<rgrid, 256, 0, st>>>(b_dev, u_dev, h->w, h->n, h->mx, 1, R);
+    noalloc_rhs_kernel<<<rgrid, 256, 0, st>>>(b_dev, u_dev, h->w, h->n, ldr, h->mx, 1, R);
     PIDE_CUDA_TRY(cudaGetLastError());
-    noalloc_gemv_kernel<<<ggrid, 256, 0, st>>>(h->inv, h->inv_lo, h->row_scale, fmt, h->ld,
-                                               h->n, B, R, u_dev, 1);
+    PIDE_TRY(launch_noalloc_gemv(h, R, ldr, B, u_dev, true, corrected(k + 1), st));
     PIDE_CUDA_TRY(cudaGetLastError());
   }
   return PIDE_OK;

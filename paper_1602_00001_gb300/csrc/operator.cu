@@ -286,6 +286,26 @@ __global__ void check_kernel(double* colmax, const double* colmax_b, int B, doub
   }
 }
 
+// Refinement record: *slot = max over columns of max|r_c| / max|f_c| for the
+// residual the last tracked launch wrote into colmax (a zero column counts its
+// absolute residual); reset: clear colmax for the next sweep.
+__global__ void record_kernel(double* colmax, const double* colmax_b, int B, double* slot,
+                              int reset, const uint32_t* flags) {
+  __shared__ double red[32];
+  if (flags[FLAG_DONE]) return;
+  double worst = 0.0;
+  for (int c = threadIdx.x; c < B; c += blockDim.x) {
+    const double den = colmax_b[c];
+    worst = fmax(worst, den > 0.0 ? colmax[c] / den : colmax[c]);
+  }
+  worst = block_max(worst, red);
+  if (threadIdx.x == 0) *slot = worst;
+  if (reset) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < B; c += blockDim.x) colmax[c] = 0.0;
+  }
+}
+
 // Column maxima of |f| (the prep right side) without writing R.
 __global__ void colmax_b_kernel(const double* __restrict__ b, int n, int mode,
                                 const double* __restrict__ dinv, const double* __restrict__ lift,
@@ -508,6 +528,14 @@ pide_status launch_residual_persistent(pide_ctx* c, const double* b, const doubl
 pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st) {
   ProfScope ps(c, st, 3);
   check_kernel<<<1, 256, 0, st>>>(c->colmax, c->colmax + c->ws_B, B, tol, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
+
+pide_status launch_record(pide_ctx* c, int B, double* slot, bool reset, cudaStream_t st) {
+  ProfScope ps(c, st, 3);
+  record_kernel<<<1, 256, 0, st>>>(c->colmax, c->colmax + c->ws_B, B, slot, reset ? 1 : 0,
+                                   c->flags);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }

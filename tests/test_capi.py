@@ -186,3 +186,33 @@ def test_binding_precisions_and_tuning_keys_match_the_header():
     assert {("PIDE_" + k.upper()): v for k, v in binding.PRECISIONS.items()} == prec
     keys = _header_enum("pide_tune_key")
     assert {("PIDE_TUNE_" + k.upper()): v for k, v in binding.Solver.TUNE_KEYS.items()} == keys
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures carry the header's field offsets and sizes (a C
+    program compiled against include/pide.h prints them)."""
+    import os
+    import subprocess
+    from paper_1602_00001_gb300 import binding
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"pide_info": binding.Info, "pide_handle_info": binding.HandleInfo,
+               "pide_auto_candidate": binding.AutoCandidate,
+               "pide_auto_report": binding.AutoReport, "pide_grid": binding.Grid,
+               "pide_grid3": binding.Grid3, "pide_profile": binding.Profile}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pide.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, value = line.split()
+        cls = structs[cname]
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (cname, field, got, value)
