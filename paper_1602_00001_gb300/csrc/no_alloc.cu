@@ -140,26 +140,26 @@ __device__ __forceinline__ void to_float(const uint4& raw, float (&a)[Store<KIND
 
 // The second term of a row, V e4m3 entries at the same positions: the FP8X2
 // lo term (same row scale) or the e4m3 correction term (its own row scale).
+// load_second fetches its V bytes, second_term converts them.
 template <int V>
-__device__ __forceinline__ void second_term(const uint8_t* p, float (&a)[V]) {
+__device__ __forceinline__ uint4 load_second(const uint8_t* p) {
   if constexpr (V == 16) {
-    const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(p));
-    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) a[4 * i + k] = e4m3_value(w[i] >> (8 * k));
+    return __ldcs(reinterpret_cast<const uint4*>(p));
   } else if constexpr (V == 8) {
-    const uint2 raw = __ldcs(reinterpret_cast<const uint2*>(p));
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      a[k] = e4m3_value(raw.x >> (8 * k));
-      a[4 + k] = e4m3_value(raw.y >> (8 * k));
-    }
+    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+    return make_uint4(v.x, v.y, 0u, 0u);
+  } else if constexpr (V == 4) {
+    return make_uint4(__ldcs(reinterpret_cast<const unsigned int*>(p)), 0u, 0u, 0u);
   } else {
-#pragma unroll
-    for (int k = 0; k < V; ++k) a[k] = e4m3_value(p[k]);
+    return make_uint4((uint32_t)p[0] | ((uint32_t)p[1] << 8), 0u, 0u, 0u);
   }
+}
+
+template <int V>
+__device__ __forceinline__ void second_term(const uint4& raw, float (&a)[V]) {
+  const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+  for (int k = 0; k < V; ++k) a[k] = e4m3_value(w[k >> 2] >> (8 * (k & 3)));
 }
 
 // u[c][p] (=|+=) scale_p * sum_q A[p][q] R[c][q] for the ROWS rows of each warp.
@@ -186,17 +186,23 @@ __global__ void __launch_bounds__(256) noalloc_gemv_kernel(
       ratio[r] = second ? (second_scale ? second_scale[p] / s : 1.0f) : 0.0f;
     }
     for (int q = lane * V; q < ldr; q += 32 * V) {
+      // every row's loads are issued before any is converted
+      uint4 raw[ROWS];
+      uint4 raw2[ROWS];
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const size_t e = (size_t)min(p0 + r, n - 1) * ld + q;
+        raw[r] = __ldcs(reinterpret_cast<const uint4*>(
+            reinterpret_cast<const uint8_t*>(inv) + e * (16 / V)));
+        if (second) raw2[r] = load_second<V>(second + e);
+      }
       float a[ROWS][V];
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
-        const int p = min(p0 + r, n - 1);
-        const size_t e = (size_t)p * ld + q;
-        const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(
-            reinterpret_cast<const uint8_t*>(inv) + e * (16 / V)));
-        to_float<KIND>(raw, a[r]);
+        to_float<KIND>(raw[r], a[r]);
         if (second) {
           float t[V];
-          second_term<V>(second + e, t);
+          second_term<V>(raw2[r], t);
 #pragma unroll
           for (int v = 0; v < V; ++v) a[r][v] = fmaf(ratio[r], t[v], a[r][v]);
         }

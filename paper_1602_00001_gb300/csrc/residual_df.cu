@@ -464,8 +464,11 @@ __global__ void prep_df_bf16_kernel(const double* __restrict__ b, int n, int ldr
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const double bp = bc[p];
     __nv_bfloat16 q;
+    // |f| for the column maximum, to FP32 accuracy (not the BF16 value)
+    float af = 0.f;
     if (!lift) {
       q = bf16_of_f64(bp);
+      if (track) af = fabsf(__double2float_rn(bp));
     } else {
       float bh, bl, lh, ll;
       const double lp = lift[p];
@@ -477,12 +480,14 @@ __global__ void prep_df_bf16_kernel(const double* __restrict__ b, int n, int ldr
         df_add(bh, bl, lh, ll);
         const float s = __fadd_rn(bh, bl);
         q = bf16_of_pair(s, __fsub_rn(bl, __fsub_rn(s, bh)));
+        af = fabsf(s);
       } else {
         q = bf16_of_f64_slow(bp + lp);
+        if (track) af = fabsf(__double2float_rn(bp + lp));
       }
     }
     R[(size_t)col * ldr + p] = q;
-    if (track) mx = fmaxf(mx, fabsf(__bfloat162float(q)));
+    if (track) mx = fmaxf(mx, af);
   }
   if (track) {
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
