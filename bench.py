@@ -326,9 +326,23 @@ def batched_workload(args):
         us.append(torch.empty_like(bd))
     total_rhs = sum(b.shape[0] for b in bs)
     sweeps = args.sweeps if args.sweeps >= 0 else 6
-    # an FP32 store converges in far fewer sweeps than a BF16 one: cap it at 2
+    # an FP32 store (TF32 on the tensor cores, 11 significant bits like FP16)
+    # converges in far fewer sweeps than a BF16 one: cap it at 2
     caps = [min(2, sweeps) if sv.precision == "fp32" else sweeps for sv in solvers]
-    plan = BatchPlan(solvers, bs, us, sweeps_per_problem=caps)
+    # the autotuner times the plan's knobs (tensor-core column tile, FP32 on the
+    # tensor cores or the SIMT tiles) on one problem of each (precision, n, B)
+    # bucket, outside the timed region; the plan is built from its cache
+    from paper_1602_00001_gb300 import autotune as AT
+    cache = AT.TuneCache(os.path.join(ROOT, "_build", "pide_tune_bench.json"))
+    t_tune = time.perf_counter()
+    tuned = {}
+    for sv, b, u, cap in zip(solvers, bs, us, caps):
+        key = AT.batch_key_for(sv.n, b.shape[0], sv.precision)
+        if key not in tuned:
+            tuned[key] = AT.tune_batch(sv, b, u, sweeps=cap, cache=cache, save=False)[0]
+    t_tune = time.perf_counter() - t_tune
+    plan = BatchPlan(solvers, bs, us, sweeps_per_problem=caps, tune_cache=cache)
+    pinfo = plan.info()
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         plan.run(sweeps, use_graph=True, stream=st)
@@ -345,8 +359,7 @@ def batched_workload(args):
         for sv, b, u, kc in zip(solvers, bs, us, caps):
             sv.apply(b, u, sweeps=kc)
     ms_loop = _evt_time(loop, max(3, args.steps // 4))
-    kinds = int(any(sv.precision == "fp32" for sv in solvers)) + int(any(sv.precision == "bf16" for sv in solvers))
-    launches = 1 + (1 + sweeps) * kinds + sweeps
+    launches = 1 + (1 + sweeps) * pinfo["apply_launches"] + sweeps
     line = {"metric": "RHS solves/s, 64 uneven grids (batched)", "value": total_rhs / (ms_batched * 1e-3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": ms_batched,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32+bf16",
@@ -356,6 +369,8 @@ def batched_workload(args):
                        "sizes": [int(p[0]) for p in probs]},
             "per_problem_loop": {"ms_per_step": ms_loop, "value": total_rhs / (ms_loop * 1e-3)},
             "speedup_vs_loop": ms_loop / ms_batched, "gpu_launches_per_step": launches,
+            "plan": pinfo, "tuning": {"chosen": tuned, "seconds": t_tune,
+                                      "source": "autotune.tune_batch per (precision, n, B) bucket"},
             "roofline": batched_roofline(solvers, bs, caps, ms_batched),
             "accuracy": {"max_rel_err_eq6_vs_oracle_4_problems": max(errs)}}
     print(json.dumps(line))

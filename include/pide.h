@@ -354,6 +354,18 @@ pide_status pide_batch_create(const pide_handle* hs, int32_t nprob, const double
                               double* const* u, const int32_t* Bs, const int32_t* sweeps_k,
                               pide_batch_handle* out);
 pide_status pide_batch_run(pide_batch_handle p, int32_t sweeps, int32_t use_graph, void* stream);
+
+/* The shapes a plan launches (what the problems' PIDE_TUNE_BATCH_* knobs chose). */
+typedef struct {
+  int32_t nprob;
+  int32_t simt_items;          /* SIMT tile items per apply phase */
+  int32_t tc_items;            /* grouped tensor-core items per apply phase */
+  int32_t tc_items_bn[3];      /* of those, items with column tiles 32, 64, 128 wide */
+  int32_t simt_problems_tn[3]; /* problems on SIMT tiles 16, 32, 64 columns wide */
+  int32_t tf32_problems;       /* FP32 problems contracted on the TF32 tensor cores */
+  int32_t apply_launches;      /* apply launches per phase */
+} pide_batch_info;
+pide_status pide_batch_get_info(pide_batch_handle p, pide_batch_info* out);
 void pide_batch_destroy(pide_batch_handle p);
 pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob, const double* const* b,
                                double* const* u, const int32_t* Bs, int32_t sweeps,
@@ -458,7 +470,18 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_GEMM_U_HINT     tensor-core GEMM epilogues: 1 (default) = load and store u with
  *                           an L2 evict-first hint (keeps the streamed inverse's lines in L2:
  *                           at 198^2, B = 1024, DRAM reads per accumulating launch 6.5 -> 5.2 GB,
- *                           same time), 0 = plain */
+ *                           same time), 0 = plain
+ * Batched plans read three more knobs of each problem's handle when they are created:
+ *   PIDE_TUNE_BATCH_TC        FP32 stores: 1 (default) = contract on the tensor cores as TF32
+ *                           (kind::tf32: 10 explicit mantissa bits of each stored entry and
+ *                           right-hand-side value, FP32 accumulate) in the grouped launch, the
+ *                           FP64 residual refining the result; 0 = the FP32 SIMT tiles (FP32
+ *                           products)
+ *   PIDE_TUNE_BATCH_BN        grouped tensor-core launch: column-tile width 32, 64 or 128
+ *                           (0 = default 64); each width present in a plan is one launch per
+ *                           phase
+ *   PIDE_TUNE_BATCH_TN        SIMT tiles: width 16, 32 or 64 columns (0 = default: the narrowest
+ *                           covering the problem's B) */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -474,7 +497,10 @@ typedef enum {
   PIDE_TUNE_GEMM_A_HINT = 11,
   PIDE_TUNE_RESID_PREFETCH = 12,
   PIDE_TUNE_CORR_MASK = 13,
-  PIDE_TUNE_GEMM_U_HINT = 14
+  PIDE_TUNE_GEMM_U_HINT = 14,
+  PIDE_TUNE_BATCH_TC = 15,
+  PIDE_TUNE_BATCH_BN = 16,
+  PIDE_TUNE_BATCH_TN = 17
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

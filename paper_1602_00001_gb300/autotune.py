@@ -157,3 +157,75 @@ def apply_cached(solver, B: int, cache: TuneCache | None = None, gpu: str | None
         return False
     solver.set_tuning(**ent["knobs"])
     return True
+
+
+# ---------------------------------------------------------------- batched plans
+# The knobs a batched plan reads from each problem's handle when it is created:
+# for BF16 problems and FP32 problems on the TF32 tensor cores the grouped
+# launch's column-tile width (32, 64, 128); for FP32 problems also the SIMT
+# tiles (FP32 products, width 16, 32, 64) instead of the tensor cores.
+
+
+def batch_key_for(n: int, B: int, precision: str) -> str:
+    return f"batch|{precision}|{bucket_n(n)}|{bucket_b(B)}"
+
+
+def batch_candidates(precision: str, B: int):
+    for bn in (32, 64, 128):
+        if bn >= 2 * max(B, 16) and bn > 32:
+            continue               # wider than twice the columns: idle tensor columns
+        yield {"batch_tc": 1, "batch_bn": bn}
+    if precision == "fp32":
+        for tn in (16, 32, 64):
+            yield {"batch_tc": 0, "batch_tn": tn}
+
+
+def batch_plan_timer(solver, b, u, sweeps: int, reps: int = 5):
+    """Timer for one problem alone in a plan: CUDA events around `reps` runs
+    (a new plan per candidate, since plans read the knobs when created)."""
+    import torch
+    from .binding import BatchPlan
+
+    def t(knobs):
+        solver.set_tuning(**knobs)
+        plan = BatchPlan([solver], [b], [u])
+        plan.run(sweeps=sweeps, use_graph=False)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            plan.run(sweeps=sweeps, use_graph=False)
+        e.record()
+        torch.cuda.synchronize()
+        plan.close()
+        return s.elapsed_time(e) / reps
+
+    return t
+
+
+def tune_batch(solver, b, u, sweeps: int = 2, cache: TuneCache | None = None,
+               gpu: str | None = None, timer=None, save: bool = True):
+    """Tune the batched-plan knobs of one problem (its solver, right-hand sides
+    b and output u, [B][n] device tensors); the winner is set on the solver and
+    cached under the (precision, n bucket, B bucket) key.  Returns (knobs, ms)."""
+    B = b.reshape(-1, solver.n).shape[0]
+    cache = cache or TuneCache()
+    gpu = gpu or _gpu_name()
+    timer = timer or batch_plan_timer(solver, b, u, sweeps)
+    best, ms, _ = search(batch_candidates(solver.precision, B), timer)
+    cache.put(gpu, batch_key_for(solver.n, B, solver.precision), best, ms)
+    if save:
+        cache.save()
+    solver.set_tuning(**best)
+    return best, ms
+
+
+def apply_cached_batch(solver, B: int, cache: TuneCache | None = None,
+                       gpu: str | None = None) -> bool:
+    """Set the cached batched-plan knobs for (solver, B) if the cache has them."""
+    cache = cache or TuneCache()
+    ent = cache.get(gpu or _gpu_name(), batch_key_for(solver.n, B, solver.precision))
+    if not ent:
+        return False
+    solver.set_tuning(**ent["knobs"])
+    return True

@@ -56,6 +56,13 @@ class AutoReport(ctypes.Structure):
                 ("chosen", ctypes.c_int32), ("cand", AutoCandidate * 6)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nprob", ctypes.c_int32), ("simt_items", ctypes.c_int32),
+                ("tc_items", ctypes.c_int32), ("tc_items_bn", ctypes.c_int32 * 3),
+                ("simt_problems_tn", ctypes.c_int32 * 3), ("tf32_problems", ctypes.c_int32),
+                ("apply_launches", ctypes.c_int32)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32 * 4), ("ms", ctypes.c_double * 4)]
 
@@ -86,6 +93,7 @@ _SIGS = {
     "pide_batch_create": (_I, [_P, _I, _P, _P, _P, _P, ctypes.POINTER(_P)]),
     "pide_batch_run": (_I, [_P, _I, _I, _P]),
     "pide_batch_destroy": (None, [_P]),
+    "pide_batch_get_info": (_I, [_P, ctypes.POINTER(BatchInfo)]),
     "pide_reserve": (_I, [_P, _I]),
     "pide_apply_noalloc": (_I, [_P, _P, _P, _I, _I, _P]),
     "pide_save": (_I, [_P, ctypes.c_char_p]),
@@ -363,7 +371,7 @@ class Solver:
                  "resid_emul": 8, "resid_shape": 9,
                  "gemm_2cta": 10, "gemm_a_hint": 11,
                  "resid_prefetch": 12, "corr_mask": 13,
-                 "gemm_u_hint": 14}
+                 "gemm_u_hint": 14, "batch_tc": 15, "batch_bn": 16, "batch_tn": 17}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():
@@ -486,9 +494,15 @@ class BatchPlan:
     """pide_batch_create / run / destroy: the uneven-grid batched apply with
     optional CUDA-graph replay (buffers are fixed in the plan)."""
 
-    def __init__(self, solvers, bs, us, sweeps_per_problem=None):
+    def __init__(self, solvers, bs, us, sweeps_per_problem=None, tune_cache=None):
+        """tune_cache: an autotune.TuneCache whose batched-plan entries are set
+        on each solver (by precision, n and B bucket) before the plan is built."""
         self.lib = load_library()
         k = len(solvers)
+        if tune_cache is not None:
+            from . import autotune
+            for s, b in zip(solvers, bs):
+                autotune.apply_cached_batch(s, b.reshape(-1, s.n).shape[0], cache=tune_cache)
         self._keep = (solvers, bs, us)
         sk = None
         if sweeps_per_problem is not None:
@@ -501,6 +515,17 @@ class BatchPlan:
         _check(self.lib.pide_batch_create(hs, k, bp, up, Bs, sk, ctypes.byref(out)),
                "pide_batch_create")
         self.plan = out
+
+    def info(self) -> dict:
+        """The shapes the plan launches (pide_batch_get_info)."""
+        bi = BatchInfo()
+        _check(self.lib.pide_batch_get_info(self.plan, ctypes.byref(bi)), "pide_batch_get_info")
+        return {"nprob": bi.nprob, "simt_items": bi.simt_items, "tc_items": bi.tc_items,
+                "tc_items_bn": {32: bi.tc_items_bn[0], 64: bi.tc_items_bn[1],
+                                128: bi.tc_items_bn[2]},
+                "simt_problems_tn": {16: bi.simt_problems_tn[0], 32: bi.simt_problems_tn[1],
+                                     64: bi.simt_problems_tn[2]},
+                "tf32_problems": bi.tf32_problems, "apply_launches": bi.apply_launches}
 
     def run(self, sweeps: int = 2, use_graph: bool = True, stream=None):
         _check(self.lib.pide_batch_run(self.plan, int(sweeps), 1 if use_graph else 0,

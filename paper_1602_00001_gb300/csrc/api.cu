@@ -1116,6 +1116,18 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value < 0 || value > 1) break;
       h->gemm_u_hint = value;
       return PIDE_OK;
+    case PIDE_TUNE_BATCH_TC:
+      if (value != 0 && value != 1) break;
+      h->batch_tc = value;
+      return PIDE_OK;
+    case PIDE_TUNE_BATCH_BN:
+      if (value != 0 && value != 32 && value != 64 && value != 128) break;
+      h->batch_bn = value;
+      return PIDE_OK;
+    case PIDE_TUNE_BATCH_TN:
+      if (value != 0 && value != 16 && value != 32 && value != 64) break;
+      h->batch_tn = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -1142,6 +1154,9 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_RESID_PREFETCH: *value = h->resid_prefetch; return PIDE_OK;
     case PIDE_TUNE_CORR_MASK: *value = h->corr_mask; return PIDE_OK;
     case PIDE_TUNE_GEMM_U_HINT: *value = h->gemm_u_hint; return PIDE_OK;
+    case PIDE_TUNE_BATCH_TC: *value = h->batch_tc; return PIDE_OK;
+    case PIDE_TUNE_BATCH_BN: *value = h->batch_bn; return PIDE_OK;
+    case PIDE_TUNE_BATCH_TN: *value = h->batch_tn; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

@@ -338,25 +338,41 @@ __global__ void __launch_bounds__(256) batched_vec_kernel(const BatchProb* __res
 
 
 // ---------------------------------------------------------------------------
-// BF16 problems: one grouped tcgen05 launch.  Same pipeline as the main
-// tensor-core apply (TMA producer warp, single-thread MMA issuer, four
+// BF16 and FP32 problems: grouped tcgen05 launches.  Same pipeline as the
+// main tensor-core apply (TMA producer warp, single-thread MMA issuer, four
 // epilogue warps, 2 TMEM accumulators), but every (problem, 128-row tile,
-// 64-column tile) item takes its TMA maps from a device array of per-problem
-// descriptors, so problems of any size share the launch.
+// BN-column tile) item takes its TMA maps from a device array of per-problem
+// descriptors, so problems of any size share the launch.  A BF16 problem
+// contracts on kind::f16 (64 K values per 128-byte stage row); an FP32
+// problem on kind::tf32 (32 K values per row): the tensor cores read each FP32
+// entry of the stored inverse and of the FP32 right-hand side with TF32's 10
+// explicit mantissa bits, and the refinement's FP64 residual wins the rest
+// back.  The column-tile width BN (32, 64 or 128) is per problem (the
+// PIDE_TUNE_BATCH_BN knob, which the autotuner sets); each width present in a
+// plan is one launch per phase.
 struct alignas(64) GroupProb {
-  CUtensorMap tmA;      // stored L^-1 of the problem (box 64 x 128)
-  CUtensorMap tmR;      // its right-hand-side workspace (box 64 x 64)
+  CUtensorMap tmA;      // stored L^-1 of the problem (box 128 bytes x 128 rows)
+  CUtensorMap tmR;      // its right-hand-side workspace (box 128 bytes x BN rows)
   double* u;
   int n, B, num_kb, cap;
+  int tf32;             // 1: FP32 store on kind::tf32, 0: BF16 on kind::f16
 };
 
-constexpr int GBN = 64, GSTAGES = 8;
-constexpr int G_A_BYTES = 128 * 128, G_B_BYTES = GBN * 128;
+constexpr int G_A_BYTES = 128 * 128;
+constexpr int GBN_DEFAULT = 64;
+// stages of the grouped kernel for a column-tile width (~160-192 KB of shared memory)
+constexpr int g_stages(int bn) { return bn >= 128 ? 6 : 8; }
+constexpr size_t g_smem(int bn) {
+  return 1024 + (size_t)g_stages(bn) * (G_A_BYTES + bn * 128) + 256;
+}
 
+template <int GBN>
 __global__ void __launch_bounds__(192, 1) grouped_gemm_kernel(const GroupProb* __restrict__ probs,
                                                               const int4* __restrict__ items,
                                                               int nitems, int accumulate, int phase,
                                                               uint32_t* __restrict__ flags) {
+  constexpr int GSTAGES = g_stages(GBN);
+  constexpr int G_B_BYTES = GBN * 128;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -409,9 +425,11 @@ __global__ void __launch_bounds__(192, 1) grouped_gemm_kernel(const GroupProb* _
           ok = false;
           break;
         }
+        // 128 bytes of K per stage row: 64 BF16 or 32 FP32 values
+        const int kx = P->tf32 ? kb * 32 : kb * 64;
         mbar_expect_tx(&full[st], G_A_BYTES + G_B_BYTES);
-        tma_load_2d_hint(sA + st * G_A_BYTES, mA, &full[st], kb * 64, w.y * 128, pol_a);
-        tma_load_2d(sB + st * G_B_BYTES, mR, &full[st], kb * 64, w.z * GBN);
+        tma_load_2d_hint(sA + st * G_A_BYTES, mA, &full[st], kx, w.y * 128, pol_a);
+        tma_load_2d(sB + st * G_B_BYTES, mR, &full[st], kx, w.z * GBN);
         issued |= 1u << st;
         issued_ph = (issued_ph & ~(1u << st)) | (ph << st);
         if (++st == GSTAGES) {
@@ -428,8 +446,12 @@ __global__ void __launch_bounds__(192, 1) grouped_gemm_kernel(const GroupProb* _
         if (issued & (1u << q)) mbar_wait_bounded(&full[q], (issued_ph >> q) & 1u, &never);
     }
   } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GBN >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
+    // instruction descriptors: F32 accumulator (bits 4-5 = 1), A and B formats
+    // (bits 7-9, 10-12: 1 = BF16 for kind::f16, 2 = TF32 for kind::tf32), both
+    // K-major, N / 8 (bits 17-22), M / 16 (bits 24-28)
+    const uint32_t shape = ((uint32_t)(GBN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t idesc_bf16 = (1u << 4) | (1u << 7) | (1u << 10) | shape;
+    const uint32_t idesc_tf32 = (1u << 4) | (2u << 7) | (2u << 10) | shape;
     int st = 0, acc = 0;
     uint32_t ph = 0, acc_ph = 0;
     bool ok = true;
@@ -452,10 +474,18 @@ __global__ void __launch_bounds__(192, 1) grouped_gemm_kernel(const GroupProb* _
         tc_fence_after();
         const uint32_t a_addr = smem_u32(sA + st * G_A_BYTES);
         const uint32_t b_addr = smem_u32(sB + st * G_B_BYTES);
+        // four MMAs per stage, 32 bytes of K each (K = 16 BF16 or 8 TF32)
+        if (P->tf32) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
-                  (kb > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < 4; ++k)
+            mma_tf32(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
+                     idesc_tf32, (kb > 0 || k > 0) ? 1u : 0u);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
+                    idesc_bf16, (kb > 0 || k > 0) ? 1u : 0u);
+        }
         mma_commit(&empty[st]);
         if (++st == GSTAGES) {
           st = 0;
@@ -534,9 +564,14 @@ __global__ void __launch_bounds__(192, 1) grouped_gemm_kernel(const GroupProb* _
 
 struct pide_batch {
   int nprob = 0, nitems = 0, ncolitems = 0;
-  int ngitems = 0;                     // grouped tensor-core items (BF16 problems)
+  // grouped tensor-core items (BF16 and FP32 problems), one list per column-tile
+  // width BN = 32, 64, 128
+  int ngitems = 0;
+  int ngitems_bn[3] = {0, 0, 0};
   pide::GroupProb* d_gprobs = nullptr;
-  int4* d_gitems = nullptr;
+  int4* d_gitems_bn[3] = {nullptr, nullptr, nullptr};
+  int nsimt_shape[3] = {0, 0, 0};      // SIMT problems per tile width (16, 32, 64 columns)
+  int ntf32 = 0;                       // FP32 problems on the TF32 tensor cores
   uint32_t* d_flags = nullptr;
   pide::BatchProb* d_probs = nullptr;
   int4* d_items = nullptr;
@@ -561,7 +596,8 @@ static void batch_free(pide_batch* p) {
   if (p->d_colitems) cudaFree(p->d_colitems);
   if (p->d_counter) cudaFree(p->d_counter);
   if (p->d_gprobs) cudaFree(p->d_gprobs);
-  if (p->d_gitems) cudaFree(p->d_gitems);
+  for (int4* q : p->d_gitems_bn)
+    if (q) cudaFree(q);
   if (p->d_flags) cudaFree(p->d_flags);
   delete p;
 }
@@ -583,7 +619,7 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
   pide_batch* p = new pide_batch();
   std::vector<BatchProb> probs(nprob);
   struct Item { int prob, mt, ct; double cost; int shape = 0; };
-  std::vector<Item> items, gitems;
+  std::vector<Item> items, gitems_bn[3];
   std::vector<GroupProb> gprobs;
   std::vector<int> gindex(nprob, -1);
   std::vector<int2> colitems;
@@ -615,13 +651,27 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
     probs[k] = BatchProb{h->inv, h->w, b[k], u[k], (float*)h->R, h->ld, h->n, h->mx, Bs[k],
                          h->prec == PIDE_FP32 ? 0 : 1,
                          sweeps_k ? (sweeps_k[k] < 0 ? 0 : sweeps_k[k]) : 1 << 30, 0};
-    if (h->prec == PIDE_BF16 && h->tmA_ok && Bs[k] > 0) {
-      // tensor cores: (problem, 128-row tile, 64-column tile) items with this problem's maps
+    const bool tc_bf16 = h->prec == PIDE_BF16 && h->tmA_ok;
+    const bool tc_tf32 = h->prec == PIDE_FP32 && h->batch_tc;
+    if ((tc_bf16 || tc_tf32) && Bs[k] > 0) {
+      // tensor cores: (problem, 128-row tile, BN-column tile) items with this problem's
+      // maps; BN from the problem's knob (0: 64)
+      const int bn = h->batch_bn > 0 ? h->batch_bn : GBN_DEFAULT;
+      const int bcode = bn == 32 ? 0 : (bn == 64 ? 1 : 2);
       GroupProb g;
       std::memset(&g, 0, sizeof(g));
-      g.tmA = h->tmA;
-      pide_status es = encode_2d(&g.tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, h->R, h->n, h->ws_B,
-                                 (uint64_t)h->ld * 2, 64, GBN);
+      pide_status es = PIDE_OK;
+      if (tc_bf16) {
+        g.tmA = h->tmA;
+        es = encode_2d(&g.tmR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, h->R, h->n, h->ws_B,
+                       (uint64_t)h->ld * 2, 64, bn);
+      } else {
+        es = encode_2d(&g.tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, h->inv, h->n, h->n,
+                       (uint64_t)h->ld * 4, 32, 128);
+        if (es == PIDE_OK)
+          es = encode_2d(&g.tmR, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, h->R, h->n, h->ws_B,
+                         (uint64_t)h->ld * 4, 32, bn);
+      }
       if (es != PIDE_OK) {
         batch_free(p);
         return es;
@@ -629,17 +679,23 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
       g.u = u[k];
       g.n = h->n;
       g.B = Bs[k];
-      g.num_kb = (h->n + 63) / 64;
+      g.tf32 = tc_tf32 ? 1 : 0;
+      p->ntf32 += g.tf32;
+      g.num_kb = tc_tf32 ? (h->n + 31) / 32 : (h->n + 63) / 64;
       g.cap = probs[k].pad;
-      probs[k].rbf16 = 1;
+      probs[k].rbf16 = tc_bf16 ? 1 : 0;
       gindex[k] = (int)gprobs.size();
       gprobs.push_back(g);
-      const int mt = (h->n + 127) / 128, ct = (Bs[k] + GBN - 1) / GBN;
+      const int mt = (h->n + 127) / 128, ct = (Bs[k] + bn - 1) / bn;
+      // cost: K bytes streamed per item (an FP32 K block holds half the values)
       for (int i = 0; i < mt; ++i)
-        for (int j = 0; j < ct; ++j) gitems.push_back({gindex[k], i, j, (double)g.num_kb});
+        for (int j = 0; j < ct; ++j) gitems_bn[bcode].push_back({gindex[k], i, j, (double)g.num_kb});
     } else if (Bs[k] > 0) {
-      // SIMT: the narrowest tile shape that covers B (16, 32 or 64 columns)
-      const int code = Bs[k] <= 16 ? 0 : (Bs[k] <= 32 ? 1 : 2);
+      // SIMT: the tile width from the problem's knob, else the narrowest that
+      // covers B (16, 32 or 64 columns)
+      int code = Bs[k] <= 16 ? 0 : (Bs[k] <= 32 ? 1 : 2);
+      if (h->batch_tn > 0) code = h->batch_tn == 16 ? 0 : (h->batch_tn == 32 ? 1 : 2);
+      p->nsimt_shape[code] += 1;
       const int tn = code == 0 ? 16 : (code == 1 ? 32 : 64), tm = SB_OUT / tn;
       const int mt = (h->n + tm - 1) / tm, ct = (Bs[k] + tn - 1) / tn;
       for (int i = 0; i < mt; ++i)
@@ -655,11 +711,14 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
                    [](const Item& a, const Item& c) { return a.cost > c.cost; });
   std::vector<int4> it4(items.size());
   for (size_t i = 0; i < items.size(); ++i) it4[i] = make_int4(items[i].prob, items[i].mt, items[i].ct, items[i].shape);
-  std::stable_sort(gitems.begin(), gitems.end(),
-                   [](const Item& a, const Item& c) { return a.cost > c.cost; });
-  std::vector<int4> g4(gitems.size());
-  for (size_t i = 0; i < gitems.size(); ++i) g4[i] = make_int4(gitems[i].prob, gitems[i].mt, gitems[i].ct, 0);
-  p->ngitems = (int)g4.size();
+  std::vector<int4> g4[3];
+  for (int q = 0; q < 3; ++q) {
+    std::stable_sort(gitems_bn[q].begin(), gitems_bn[q].end(),
+                     [](const Item& a, const Item& c) { return a.cost > c.cost; });
+    for (const Item& t : gitems_bn[q]) g4[q].push_back(make_int4(t.prob, t.mt, t.ct, 0));
+    p->ngitems_bn[q] = (int)g4[q].size();
+    p->ngitems += p->ngitems_bn[q];
+  }
   p->nprob = nprob;
   p->nitems = (int)it4.size();
   p->ncolitems = (int)colitems.size();
@@ -679,13 +738,20 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
   if (!colitems.empty() && (e = cudaMemcpy(p->d_colitems, colitems.data(), colitems.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if (!gprobs.empty()) {
     if ((e = cudaMalloc((void**)&p->d_gprobs, gprobs.size() * sizeof(GroupProb))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc((void**)&p->d_gitems, g4.size() * sizeof(int4))) != cudaSuccess) return fail(e);
+    for (int q = 0; q < 3; ++q)
+      if (!g4[q].empty() &&
+          (e = cudaMalloc((void**)&p->d_gitems_bn[q], g4[q].size() * sizeof(int4))) != cudaSuccess)
+        return fail(e);
     if ((e = cudaMalloc((void**)&p->d_flags, FLAG_COUNT * sizeof(uint32_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(p->d_flags, 0, FLAG_COUNT * sizeof(uint32_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(p->d_gprobs, gprobs.data(), gprobs.size() * sizeof(GroupProb), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemcpy(p->d_gitems, g4.data(), g4.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    const size_t smem = 1024 + (size_t)GSTAGES * (G_A_BYTES + G_B_BYTES) + 256;
-    if ((e = cudaFuncSetAttribute(grouped_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return fail(e);
+    for (int q = 0; q < 3; ++q)
+      if (!g4[q].empty() && (e = cudaMemcpy(p->d_gitems_bn[q], g4[q].data(), g4[q].size() * sizeof(int4),
+                                            cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaFuncSetAttribute(grouped_gemm_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem(32))) != cudaSuccess) return fail(e);
+    if ((e = cudaFuncSetAttribute(grouped_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem(64))) != cudaSuccess) return fail(e);
+    if ((e = cudaFuncSetAttribute(grouped_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem(128))) != cudaSuccess) return fail(e);
   }
   *out = p;
   return PIDE_OK;
@@ -700,11 +766,20 @@ static pide_status batch_apply(pide_batch* p, int phase, cudaStream_t st) {
                                                            p->d_counter + phase, phase > 0, phase, 1);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
-  if (p->ngitems > 0) {
-    const size_t smem = 1024 + (size_t)GSTAGES * (G_A_BYTES + G_B_BYTES) + 256;
-    const int grid = std::min(p->ngitems, p->num_sms);
-    grouped_gemm_kernel<<<grid, 192, smem, st>>>(p->d_gprobs, p->d_gitems, p->ngitems, phase > 0,
-                                                 phase, p->d_flags);
+  // one grouped launch per column-tile width present in the plan
+  for (int q = 0; q < 3; ++q) {
+    const int ni = p->ngitems_bn[q];
+    if (ni == 0) continue;
+    const int grid = std::min(ni, p->num_sms);
+    if (q == 0)
+      grouped_gemm_kernel<32><<<grid, 192, g_smem(32), st>>>(p->d_gprobs, p->d_gitems_bn[q], ni,
+                                                             phase > 0, phase, p->d_flags);
+    else if (q == 1)
+      grouped_gemm_kernel<64><<<grid, 192, g_smem(64), st>>>(p->d_gprobs, p->d_gitems_bn[q], ni,
+                                                             phase > 0, phase, p->d_flags);
+    else
+      grouped_gemm_kernel<128><<<grid, 192, g_smem(128), st>>>(p->d_gprobs, p->d_gitems_bn[q], ni,
+                                                               phase > 0, phase, p->d_flags);
     PIDE_CUDA_TRY(cudaGetLastError());
   }
   return PIDE_OK;
@@ -757,6 +832,25 @@ extern "C" pide_status pide_batch_run(pide_batch_handle p, int32_t sweeps, int32
     p->graph_sweeps = sweeps;
   }
   PIDE_CUDA_TRY(cudaGraphLaunch(p->exec, st));
+  return PIDE_OK;
+}
+
+extern "C" pide_status pide_batch_get_info(pide_batch_handle p, pide_batch_info* out) {
+  if (!p || !out) {
+    set_error("pide_batch_get_info: bad argument");
+    return PIDE_EINVAL;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->nprob = p->nprob;
+  out->simt_items = p->nitems;
+  out->tc_items = p->ngitems;
+  for (int q = 0; q < 3; ++q) {
+    out->tc_items_bn[q] = p->ngitems_bn[q];
+    out->simt_problems_tn[q] = p->nsimt_shape[q];
+    out->apply_launches += p->ngitems_bn[q] > 0 ? 1 : 0;
+  }
+  out->apply_launches += p->nitems > 0 ? 1 : 0;
+  out->tf32_problems = p->ntf32;
   return PIDE_OK;
 }
 

@@ -130,6 +130,10 @@ struct pide_ctx {
   int resid_emul = 1;               // refinement residual in double-float (off the FP64 pipe)
   int resid_shape = -1;             // its launch shape: -1 default (8 nodes per thread); 0..3: 4, 8, 2, 16
   int resid_prefetch = 4;           // its L2 prefetch distance in column pairs (0: none)
+  // batched plans (pide_batch_create reads them per problem; the autotuner sets them)
+  int batch_tc = 1;                 // FP32 store: 1 TF32 tensor cores, 0 FP32 SIMT tiles
+  int batch_bn = 0;                 // tensor-core column tile 32, 64 or 128 (0: 64)
+  int batch_tn = 0;                 // SIMT tile width 16, 32 or 64 (0: the narrowest covering B)
   // refinement history of a pide_apply that fills pide_info: the worst-column
   // relative residual after apply k (k < HIST_MAX), and events timing the call
   double* hist = nullptr;
@@ -447,6 +451,19 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// kind::tf32: FP32 operands in shared memory read as TF32 (10 explicit
+// mantissa bits), F32 accumulate; K = 8 per instruction (32 bytes per row,
+// the same byte step as kind::f16's K = 16).
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }

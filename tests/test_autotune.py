@@ -82,3 +82,54 @@ def test_tune_on_gpu(tmp_path):
     assert ms > 0 and s.get_tuning()["gemm_bn"] == best["gemm_bn"]
     u = s.apply(b, sweeps=3)
     assert float((u - u_ref).abs().max()) <= 1e-6 * float(u_ref.abs().max())
+
+
+@pytest.mark.parametrize("prec,B", [("fp32", 1), ("fp32", 64), ("bf16", 9)])
+def test_batch_candidates_are_valid_knobs(prec, B):
+    c = list(T.batch_candidates(prec, B))
+    assert c and all(set(k) <= {"batch_tc", "batch_bn", "batch_tn"} for k in c)
+    assert all(k["batch_bn"] in (32, 64, 128) for k in c if k.get("batch_tc") == 1)
+    assert any(k.get("batch_tc") == 0 for k in c) == (prec == "fp32")
+
+
+def test_tune_batch_caches_and_applies(tmp_path):
+    path = str(tmp_path / "tune.json")
+    s = FakeSolver()
+    s.precision = "fp32"
+
+    def timer(knobs):  # pretend the 128-wide tensor-core tiles are fastest
+        return 1.0 if knobs == {"batch_tc": 1, "batch_bn": 128} else 2.0
+
+    best, ms = T.tune_batch(s, FakeB(100), None, cache=T.TuneCache(path), gpu="GB300", timer=timer)
+    assert best == {"batch_tc": 1, "batch_bn": 128} and ms == 1.0
+    assert json.load(open(path))["GB300"]["batch|fp32|n<=65536|B<=128"]["knobs"] == best
+    s2 = FakeSolver()
+    s2.precision = "fp32"
+    assert T.apply_cached_batch(s2, 100, cache=T.TuneCache(path), gpu="GB300")
+    assert s2.knobs == best
+
+
+@pytest.mark.gpu
+def test_tuned_cache_entry_changes_the_plan_shape(tmp_path):
+    """A batched-plan entry in the tuner's cache reaches pide_batch_create: the
+    plan built with the cache launches the cached column-tile width."""
+    import torch
+    from paper_1602_00001_gb300 import build, workloads as W
+    from paper_1602_00001_gb300.binding import BatchPlan, Solver
+    build.build()
+    n = 40
+    s = Solver(n, n, 1.0 / (n - 1), W.eps_lognormal(n, n, 3), "fp32")
+    b = torch.from_numpy(W.random_interior(n, n, 2, batch=20)).cuda()
+    u = torch.empty_like(b)
+    plain = BatchPlan([s], [b], [u])
+    assert plain.info()["tc_items_bn"] == {32: 0, 64: 12, 128: 0}
+    plain.close()
+    cache = T.TuneCache(str(tmp_path / "t.json"))
+    gpu = torch.cuda.get_device_name(0)
+    cache.put(gpu, T.batch_key_for(s.n, 20, "fp32"), {"batch_tc": 1, "batch_bn": 32}, 0.1)
+    tuned = BatchPlan([s], [b], [u], tune_cache=cache)
+    assert tuned.info()["tc_items_bn"] == {32: 12, 64: 0, 128: 0}
+    tuned.close()
+    # a real tuning pass picks one of the candidates and leaves it on the solver
+    best, ms = T.tune_batch(s, b, u, sweeps=2, cache=cache, save=False)
+    assert ms > 0 and all(s.get_tuning()[k] == v for k, v in best.items())
