@@ -388,7 +388,8 @@ def batched_roofline(solvers, bs, caps, ms):
     gbs = byts / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / pk["hbm_gbs"], "traffic": None,
-            "note": "algorithmic inverse bytes over all applies of the step; FP32 problems run on the SIMT pipe"}
+            "note": "algorithmic inverse bytes over all applies of the step; FP32 problems run "
+                    "on the TF32 tensor cores unless their knob keeps the SIMT tiles"}
 
 
 def adjoint_workload(args):
