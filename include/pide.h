@@ -481,7 +481,11 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           (0 = default 64); each width present in a plan is one launch per
  *                           phase
  *   PIDE_TUNE_BATCH_TN        SIMT tiles: width 16, 32 or 64 columns (0 = default: the narrowest
- *                           covering the problem's B) */
+ *                           covering the problem's B)
+ *   PIDE_TUNE_PREP_CLUSTER    FP16 right-hand-side prep: 1 (default) = a cluster of 4 CTAs per
+ *                           column holds the column in shared memory (one HBM pass; with the
+ *                           correction term in the first apply it also writes the e4m3 copy of R),
+ *                           up to ~56K unknowns; 0 = one CTA per column reading it twice */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -500,7 +504,8 @@ typedef enum {
   PIDE_TUNE_GEMM_U_HINT = 14,
   PIDE_TUNE_BATCH_TC = 15,
   PIDE_TUNE_BATCH_BN = 16,
-  PIDE_TUNE_BATCH_TN = 17
+  PIDE_TUNE_BATCH_TN = 17,
+  PIDE_TUNE_PREP_CLUSTER = 18
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

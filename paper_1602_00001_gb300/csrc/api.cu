@@ -243,9 +243,11 @@ pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, 
                      c->prec == PIDE_FP16) &&
                     (tol <= 0 || tol >= 1e-8);
   if (rf == RF_E4M3) PIDE_TRY(launch_fp8_scales(c, b, nullptr, B, mode, lift, false, st));
-  if (rf == RF_F16) PIDE_TRY(launch_prep_f16(c, b, B, mode, lift, track, st));
+  // FP16: the prep writes the correction term's e4m3 copy of R in the same pass
+  const bool fused_corr = rf == RF_F16 && corr_at(0);
+  if (rf == RF_F16) PIDE_TRY(launch_prep_f16(c, b, B, mode, lift, track, st, fused_corr));
   else PIDE_TRY(launch_prep(c, b, B, mode, lift, rf, track, st, emul));
-  if (corr_at(0)) PIDE_TRY(launch_corr_rhs(c, B, st));
+  if (corr_at(0) && !fused_corr) PIDE_TRY(launch_corr_rhs(c, B, st));
   PIDE_TRY(launch_apply(c, B, x, false, st));
   if (corr_at(0)) PIDE_TRY(launch_apply_corr(c, B, x, st));
   for (int k = 0; k < sweeps; ++k) {
@@ -1128,6 +1130,10 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 0 && value != 16 && value != 32 && value != 64) break;
       h->batch_tn = value;
       return PIDE_OK;
+    case PIDE_TUNE_PREP_CLUSTER:
+      if (value != 0 && value != 1) break;
+      h->prep_cluster = value;
+      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -1157,6 +1163,7 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_BATCH_TC: *value = h->batch_tc; return PIDE_OK;
     case PIDE_TUNE_BATCH_BN: *value = h->batch_bn; return PIDE_OK;
     case PIDE_TUNE_BATCH_TN: *value = h->batch_tn; return PIDE_OK;
+    case PIDE_TUNE_PREP_CLUSTER: *value = h->prep_cluster; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

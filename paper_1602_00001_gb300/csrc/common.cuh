@@ -130,6 +130,7 @@ struct pide_ctx {
   int resid_emul = 1;               // refinement residual in double-float (off the FP64 pipe)
   int resid_shape = -1;             // its launch shape: -1 default (8 nodes per thread); 0..3: 4, 8, 2, 16
   int resid_prefetch = 4;           // its L2 prefetch distance in column pairs (0: none)
+  int prep_cluster = 1;             // FP16 prep: one CTA cluster per column, one HBM pass
   // batched plans (pide_batch_create reads them per problem; the autotuner sets them)
   int batch_tc = 1;                 // FP32 store: 1 TF32 tensor cores, 0 FP32 SIMT tiles
   int batch_bn = 0;                 // tensor-core column tile 32, 64 or 128 (0: 64)
@@ -207,8 +208,10 @@ pide_status launch_prep_df_bf16(pide_ctx* c, const double* b, int B, const doubl
 // FP16 right-hand sides (f16.cu): per column t_j = 2^k with max|f_j| / t_j in
 // [2^11, 2^12) into col_scale, R = fp16(f / t_j) rounded to nearest from FP64;
 // the refinement's residuals reuse t_j.
+// with_corr: also write the e4m3 copy Rc of R and its column scales (what
+// launch_corr_rhs does), in the same pass.
 pide_status launch_prep_f16(pide_ctx* c, const double* b, int B, int mode, const double* lift,
-                            bool track, cudaStream_t st);
+                            bool track, cudaStream_t st, bool with_corr = false);
 pide_status quantize_store_f16(pide_ctx* c, const double* G, cudaStream_t st);
 // Residual with a small persistent grid (num_sms * resid_ctas_per_sm blocks), for the
 // overlapped schedule; writes R only.

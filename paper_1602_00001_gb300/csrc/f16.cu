@@ -11,8 +11,12 @@
 // every scaling exact; the GEMM epilogue multiplies the FP32 accumulator by
 // s_p t_j.  The conversions round to nearest even directly from the FP64 bit
 // pattern with integer operations (no FP64 instruction, no double rounding).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "f16_round.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pide {
 
@@ -126,6 +130,97 @@ __global__ void prep_f16_kernel(const double* __restrict__ b, int n, int ldr, in
   }
 }
 
+// The same prep with a cluster of PREP_CL CTAs per column: each CTA reads its
+// slice of f from HBM once into shared memory (as FP64), the cluster agrees on
+// the column maximum through distributed shared memory, then each CTA converts
+// its slice from shared memory -- one HBM pass instead of two (the second from
+// L2) and no per-column serial chain.  With Rc it also writes the e4m3 copy of
+// R for the correction term, exactly as corr_rhs_kernel would from R: its
+// scale is max|R| / 448, and max|R| is the FP16 value of max|f| / t_j (the
+// rounding is monotone).
+constexpr int PREP_CL = 4;
+constexpr int PREP_THREADS = 512;
+
+__global__ void __cluster_dims__(PREP_CL, 1, 1) __launch_bounds__(PREP_THREADS)
+prep_f16_cluster_kernel(const double* __restrict__ b, int n, int ldr, int mode,
+                        const double* __restrict__ dinv, const double* __restrict__ lift,
+                        __half* __restrict__ R, float* __restrict__ col_scale,
+                        double* __restrict__ colmax_b, int track, int chunk,
+                        uint8_t* __restrict__ Rc, float* __restrict__ col_scale_c) {
+  extern __shared__ double sf[];            // [chunk]: this CTA's slice of f
+  __shared__ unsigned long long red[32];
+  __shared__ unsigned long long cta_max;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int col = blockIdx.y;
+  const int p0 = rank * chunk;
+  const int len = max(0, min(chunk, n - p0));
+  const double* bc = b + (size_t)col * n;
+  uint64_t mx = 0;
+  // pass 1: HBM -> shared memory, eight loads in flight per thread
+  for (int i0 = threadIdx.x; i0 < len; i0 += 8 * PREP_THREADS) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * PREP_THREADS;
+      v[u] = i < len ? rhs_value(bc, p0 + i, mode, dinv, lift) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * PREP_THREADS;
+      if (i < len) sf[i] = v[u];
+      const uint64_t a = abs_bits(v[u]);
+      mx = a > mx ? a : mx;
+    }
+  }
+  mx = block_max_u64(mx, red);
+  if (threadIdx.x == 0) cta_max = mx;
+  cluster.sync();
+  if (threadIdx.x == 0) {
+    uint64_t m = 0;
+    for (int r = 0; r < PREP_CL; ++r) {
+      const uint64_t x = *cluster.map_shared_rank(&cta_max, r);
+      m = x > m ? x : m;
+    }
+    red[0] = m;
+  }
+  // every remote read is done before any CTA of the cluster goes on (or exits)
+  cluster.sync();
+  mx = red[0];
+  const int k = pow2_scale_exp(mx, 12);
+  if (rank == 0 && threadIdx.x == 0) {
+    col_scale[col] = ldexpf(1.0f, k);
+    if (track) colmax_b[col] = __longlong_as_double((long long)mx);
+  }
+  float isc_c = 0.0f;
+  if (Rc) {
+    const float mxr = fabsf(__half2float(__ushort_as_half(
+        f16_bits_scaled(__longlong_as_double((long long)mx), k))));
+    const float t = mxr > 0.0f ? (float)((double)mxr / 448.0) : 1.0f;
+    if (rank == 0 && threadIdx.x == 0) col_scale_c[col] = t * ldexpf(1.0f, k);
+    isc_c = 1.0f / t;
+  }
+  // pass 2: shared memory -> R (pairs of FP16), and the e4m3 pairs of Rc
+  __half2* R2 = reinterpret_cast<__half2*>(R + (size_t)col * ldr + p0);
+  __nv_fp8x2_e4m3* C2 = Rc ? reinterpret_cast<__nv_fp8x2_e4m3*>(Rc + (size_t)col * ldr + p0) : nullptr;
+  for (int i = 2 * threadIdx.x; i < len; i += 2 * PREP_THREADS) {
+    const bool two = i + 1 < len;
+    const uint16_t h0 = f16_bits_scaled(sf[i], k);
+    const uint16_t h1 = two ? f16_bits_scaled(sf[i + 1], k) : (uint16_t)0;
+    if (two) {
+      R2[i >> 1] = __halves2half2(__ushort_as_half(h0), __ushort_as_half(h1));
+    } else {
+      R[(size_t)col * ldr + p0 + i] = __ushort_as_half(h0);
+    }
+    if (C2) {
+      const float v0 = __half2float(__ushort_as_half(h0)), v1 = __half2float(__ushort_as_half(h1));
+      const __nv_fp8x2_e4m3 q(make_float2(v0 * isc_c, v1 * isc_c));
+      if (two) C2[i >> 1] = q;
+      else Rc[(size_t)col * ldr + p0 + i] = (uint8_t)(q.__x & 0xFFu);
+    }
+  }
+}
+
 }  // namespace
 
 pide_status quantize_store_f16(pide_ctx* c, const double* G, cudaStream_t st) {
@@ -139,9 +234,26 @@ pide_status quantize_store_f16(pide_ctx* c, const double* G, cudaStream_t st) {
 }
 
 pide_status launch_prep_f16(pide_ctx* c, const double* b, int B, int mode, const double* lift,
-                            bool track, cudaStream_t st) {
+                            bool track, cudaStream_t st, bool with_corr) {
   if (B == 0) return PIDE_OK;
   ProfScope ps(c, st, 2);
+  // one cluster of CTAs per column while a quarter column fits a CTA's shared memory
+  const int chunk = ((c->n + PREP_CL - 1) / PREP_CL + 7) / 8 * 8;
+  const size_t smem = (size_t)chunk * sizeof(double);
+  if (c->prep_cluster && smem <= 110 * 1024 && B <= 65535 && (!with_corr || c->Rc)) {
+    PIDE_CUDA_TRY(cudaFuncSetAttribute(prep_f16_cluster_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    prep_f16_cluster_kernel<<<dim3(PREP_CL, B), PREP_THREADS, smem, st>>>(
+        b, c->n, c->ld, mode, c->dinv, lift, (__half*)c->R, c->col_scale, c->colmax + c->ws_B,
+        track ? 1 : 0, chunk, with_corr ? (uint8_t*)c->Rc : nullptr,
+        with_corr ? c->col_scale_c : nullptr);
+    PIDE_CUDA_TRY(cudaGetLastError());
+    return PIDE_OK;
+  }
+  if (with_corr) {
+    PIDE_TRY(launch_prep_f16(c, b, B, mode, lift, track, st, false));
+    return launch_corr_rhs(c, B, st);
+  }
   // 1024 threads per column: fewer columns in flight, so that the second pass
   // over a column finds it in L2
   prep_f16_kernel<<<B, 1024, 0, st>>>(b, c->n, c->ld, mode, c->dinv, lift, (__half*)c->R,

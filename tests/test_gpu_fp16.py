@@ -207,3 +207,27 @@ def test_3d_refined():
     u = s.apply(b, sweeps=2).cpu().numpy()
     ref = O3.solve(nx, ny, nz, eps, b[[0, 299]], route="band")
     assert np.max(np.abs(u[[0, 299]] - ref)) / np.max(np.abs(ref)) < 1e-6
+
+
+@pytest.mark.parametrize("prec,nx,ny,B", [("fp16_fp8", 40, 33, 300), ("fp16", 23, 61, 5),
+                                          ("fp16_fp8", 200, 200, 64)])
+def test_cluster_prep_equals_one_cta_prep(prec, nx, ny, B):
+    """The FP16 prep with a CTA cluster per column (one HBM pass, the e4m3 copy
+    of R for the correction term written in the same pass) gives bit for bit
+    the solution of the one-CTA prep followed by the separate e4m3 copy: with
+    boundary values, with a column of zeros, and for the adjoint's f = b / d."""
+    h = 1.0 / (max(nx, ny) - 1)
+    eps = W.eps_lognormal(nx, ny, seed=nx * ny)
+    b = _b(nx, ny, h, eps, B, seed=31)
+    b[B // 2] = 0.0
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal((ny, nx)))
+    s = _solver(nx, ny, h, eps, prec)
+    s.set_tuning(gemm_streamk=0)
+    outs = {}
+    for pc in (1, 0):
+        s.set_tuning(prep_cluster=pc)
+        u = s.apply(b, sweeps=1, g=g)
+        db, _ = s.backward(u.clone(), u, torch.from_numpy(b).cuda(), sweeps=1, want_deps=False)
+        outs[pc] = (u, db)
+    assert torch.equal(outs[1][0], outs[0][0]) and torch.equal(outs[1][1], outs[0][1])
+    s.close()
