@@ -356,15 +356,27 @@ __global__ void __launch_bounds__(256) residual_df_kernel(
       }
     }
   }
-  for (int i = threadIdx.x; i < L; i += 256) {
-    const int q = q0 + i;
-    float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
-    if (q >= 0 && q < n) {
-      const double va = ua[q], vb = ub[q];
-      split_marked(va, ha, la);
-      if (has_b) split_marked(vb, hb, lb);
+  // staging: STAGE_UNROLL rows of loads in flight per thread before any split
+  constexpr int STAGE_UNROLL = 4;
+  for (int i0 = threadIdx.x; i0 < L; i0 += 256 * STAGE_UNROLL) {
+    double va[STAGE_UNROLL], vb[STAGE_UNROLL];
+#pragma unroll
+    for (int j = 0; j < STAGE_UNROLL; ++j) {
+      const int q = q0 + i0 + 256 * j;
+      const bool in = i0 + 256 * j < L && q >= 0 && q < n;
+      va[j] = in ? ua[q] : 0.0;
+      vb[j] = (in && has_b) ? ub[q] : 0.0;
     }
-    su[i] = make_float4(ha, hb, la, lb);
+#pragma unroll
+    for (int j = 0; j < STAGE_UNROLL; ++j) {
+      const int i = i0 + 256 * j;
+      if (i < L) {
+        float ha, la, hb, lb;
+        split_marked(va[j], ha, la);
+        split_marked(vb[j], hb, lb);
+        su[i] = make_float4(ha, hb, la, lb);
+      }
+    }
   }
   __syncthreads();
   const float isa = (RF == RF_E4M3 || RF == RF_F16) ? 1.0f / col_scale[ca] : 1.0f;
