@@ -485,12 +485,7 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_PREP_CLUSTER    FP16 right-hand-side prep: 1 (default) = a cluster of 4 CTAs per
  *                           column holds the column in shared memory (one HBM pass; with the
  *                           correction term in the first apply it also writes the e4m3 copy of R),
- *                           up to ~56K unknowns; 0 = one CTA per column reading it twice
- *   PIDE_TUNE_GEMM_PACE       SM-pair GEMM, whole tiles: the clusters that compute the column tiles
- *                           of one 256-row slab of the inverse wait (a bounded spin on progress
- *                           words, advisory) until each other is at most this many 64-wide
- *                           k-blocks behind, so that the slab streams from DRAM once and reaches
- *                           the others from L2; 0 (default) = no pacing; 1 .. 1024 */
+ *                           up to ~56K unknowns; 0 = one CTA per column reading it twice */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -510,8 +505,7 @@ typedef enum {
   PIDE_TUNE_BATCH_TC = 15,
   PIDE_TUNE_BATCH_BN = 16,
   PIDE_TUNE_BATCH_TN = 17,
-  PIDE_TUNE_PREP_CLUSTER = 18,
-  PIDE_TUNE_GEMM_PACE = 19
+  PIDE_TUNE_PREP_CLUSTER = 18
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -548,7 +548,7 @@ extern "C" void pide_destroy(pide_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {h->sym, h->sym_lo, h->sym_scale, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
-                  h->corr, h->corr_scale, h->Rc, h->col_scale_c, h->pace,
+                  h->corr, h->corr_scale, h->Rc, h->col_scale_c,
                   h->lift, h->colmax, h->flags, h->hist, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1134,10 +1134,6 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 0 && value != 1) break;
       h->prep_cluster = value;
       return PIDE_OK;
-    case PIDE_TUNE_GEMM_PACE:
-      if (value < 0 || value > 1024) break;
-      h->gemm_pace = value;
-      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -1168,7 +1164,6 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_BATCH_BN: *value = h->batch_bn; return PIDE_OK;
     case PIDE_TUNE_BATCH_TN: *value = h->batch_tn; return PIDE_OK;
     case PIDE_TUNE_PREP_CLUSTER: *value = h->prep_cluster; return PIDE_OK;
-    case PIDE_TUNE_GEMM_PACE: *value = h->gemm_pace; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

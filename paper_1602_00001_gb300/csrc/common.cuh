@@ -110,9 +110,6 @@ struct pide_ctx {
   int gemm_a_hint = 1;              // L2 policy of the inverse's TMA loads (policy_for_a)
   int gemm_u_hint = 1;              // epilogue's u loads/stores: 0 plain, 1 L2 evict-first
   int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
-  int gemm_pace = 0;                // SM-pair GEMM: k-blocks a slab's clusters may drift apart (0: free)
-  unsigned long long* pace = nullptr;  // [max_pairs] progress words of that pacing
-  unsigned long long pace_epoch = 0;   // launch counter tagging them
   int overlap = 0;                  // residual of one column group under the GEMM of the other
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
   cudaStream_t aux = nullptr;       // low-priority stream for the overlapped residuals

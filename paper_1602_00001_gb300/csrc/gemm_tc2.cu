@@ -125,17 +125,6 @@ __device__ __forceinline__ void mma_commit_pair_local(uint64_t* bar) {
       : "memory");
 }
 
-// Progress words of the pacing between clusters (relaxed, GPU scope: the
-// values only time the loads, no data depends on them).
-__device__ __forceinline__ void pace_store(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long pace_load(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // The (tile, k-range) segments of one cluster: as in the single-SM kernel with
 // clusters in place of CTAs.
 struct SegIter2 {
@@ -185,8 +174,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                 int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                 const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-                uint32_t* __restrict__ flags, int a_hint, int u_hint,
-                unsigned long long* __restrict__ pace, unsigned long long epoch, int pace_dist) {
+                uint32_t* __restrict__ flags, int a_hint, int u_hint) {
   constexpr bool FP8 = MODE == 1 || MODE == 2;   // kind::f8f6f4 (else kind::f16)
   constexpr bool SCALED = MODE != 0;              // epilogue applies row and column scales
   constexpr bool LO = MODE == 2;
@@ -255,38 +243,11 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     bool ok = true;
     SegIter2 it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
     int tile, kb0, kb1;
-    // Pacing (pace_dist > 0, whole tiles only): the n_tiles clusters that share a
-    // 256-row slab of the inverse (consecutive cluster ids, every wave) publish
-    // how many k-blocks they have loaded; each leader waits, with a bounded spin,
-    // until its partners are at most pace_dist k-blocks behind, so that the slab's
-    // stream reaches them while it is still in L2.  Advisory only: a spin that
-    // runs out of budget switches pacing off for the rest of the launch.
-    const int G = (int)gridDim.x / 2, cid = (int)blockIdx.x / 2;
-    bool pacing = pace && pace_dist > 0 && leader && !sk && n_tiles > 1 && G % n_tiles == 0;
-    const int grp0 = (cid / n_tiles) * n_tiles;
-    long long loaded = 0;
     while (ok && it.next(tile, kb0, kb1)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
       const int arow = mt * BM2 + (int)rank * HALF;
       const int rrow = rrow0 + nt * BN2 + (int)rank * HALF;
       for (int kb = kb0; kb < kb1; ++kb) {
-        if (pacing && (loaded & 3) == 0) {
-          pace_store(&pace[cid], (epoch << 32) | (unsigned long long)loaded);
-          const long long t0 = clock64();
-          for (int j = 0; j < n_tiles && pacing; ++j) {
-            if (grp0 + j == cid) continue;
-            while (true) {
-              const unsigned long long v = pace_load(&pace[grp0 + j]);
-              const long long pl = (v >> 32) == epoch ? (long long)(v & 0xFFFFFFFFull) : -1;
-              if (pl >= loaded - pace_dist) break;
-              if (clock64() - t0 > 400000) {      // ~0.2 ms: give up pacing
-                pacing = false;
-                break;
-              }
-            }
-          }
-        }
-        ++loaded;
         if (!mbar_wait_bounded(&empty[s], ph ^ 1, abort_s)) {
           ok = false;
           break;
@@ -501,16 +462,9 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const CUtensorMap& R = corr ? c->tmRc : c->tmR;
   const float* rs = corr ? c->corr_scale : c->row_scale;
   const float* cs = corr ? c->col_scale_c + col0 : (MODE != 0 ? c->col_scale + col0 : nullptr);
-  // pacing words: one per cluster, tagged with a launch counter (never reset)
-  if (c->gemm_pace > 0 && !c->pace) {
-    PIDE_CUDA_TRY(cudaMalloc((void**)&c->pace, (size_t)G * sizeof(unsigned long long)));
-    PIDE_CUDA_TRY(cudaMemset(c->pace, 0, (size_t)G * sizeof(unsigned long long)));
-  }
-  const unsigned long long epoch = ++c->pace_epoch & 0xFFFFFFFFull;
   kern<<<2 * clusters, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, sk, u,
                                         accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint,
-                                        c->gemm_u_hint, c->gemm_pace > 0 ? c->pace : nullptr,
-                                        epoch, c->gemm_pace);
+                                c->gemm_u_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }

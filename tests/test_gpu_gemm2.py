@@ -124,23 +124,3 @@ def test_pair_stream_k_at_full_size():
     # the same FP32 sums in another order: bounded by the contraction of |Q| |R|
     d = ((u1 - u0).abs().amax(dim=1) / u0.abs().amax(dim=1)).max().item()
     assert d < 1e-4, d
-
-
-@pytest.mark.parametrize("prec", ["fp16_fp8", "bf16"])
-def test_paced_pair_gemm_is_bit_identical(prec):
-    """Pacing the clusters of a slab (PIDE_TUNE_GEMM_PACE) changes only when
-    tiles are loaded: whole-tile results are bit-identical with and without it,
-    on a step with several waves of SM-pair tiles."""
-    from paper_1602_00001_gb300.binding import Solver
-    nx = ny = 102                      # 100^2 unknowns: 40 slabs x 4 column tiles
-    h = 1.0 / 101
-    eps = W.eps_fourier(nx, ny, h, seed=4)
-    b = O.rhs_from_charge(nx, ny, h, eps, W.gaussian_blobs(nx, ny, h, 7, batch=1024))
-    s = Solver(nx, ny, h, eps, prec)
-    s.set_tuning(gemm_streamk=0)
-    outs = []
-    for pace in (0, 16, 2):
-        s.set_tuning(gemm_pace=pace)
-        outs.append(s.apply(b, sweeps=1))
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
-    s.close()
