@@ -7,7 +7,7 @@ namespace pide {
 
 // fp16 bits of v * 2^-k, rounded to nearest even from v's FP64 bits; zero and
 // FP64 subnormals give a signed zero, values beyond 65504 saturate to 65504.
-__device__ __forceinline__ uint16_t f16_bits_scaled(double v, int k) {
+__device__ __forceinline__ uint16_t f16_bits_scaled_any(double v, int k) {
   const uint64_t x = (uint64_t)__double_as_longlong(v);
   const uint16_t sign = (uint16_t)((x >> 48) & 0x8000u);
   const int eb = (int)((x >> 52) & 0x7FF);
@@ -27,6 +27,25 @@ __device__ __forceinline__ uint16_t f16_bits_scaled(double v, int k) {
   uint32_t bits = (uint32_t)q + (E >= -14 ? (uint32_t)(E + 14) << 10 : 0u);
   if (bits > 0x7BFFu) bits = 0x7BFFu;
   return (uint16_t)(sign | bits);
+}
+
+// The same, with the common case -- a normal FP16 result -- on 32-bit integer
+// operations: the 10 fraction bits are FP64 fraction bits 51..42 (bits 19..10
+// of the high word), the rounding bit is fraction bit 41 (bit 9) and the
+// sticky bits are everything below it; other cases take the general routine.
+__device__ __forceinline__ uint16_t f16_bits_scaled(double v, int k) {
+  const uint64_t x = (uint64_t)__double_as_longlong(v);
+  const uint32_t xh = (uint32_t)(x >> 32), xl = (uint32_t)x;
+  const int eb = (int)((xh >> 20) & 0x7FFu);
+  const int E = eb - 1023 - k;
+  if (eb == 0 || eb == 0x7FF || E < -14 || E > 15) return f16_bits_scaled_any(v, k);
+  uint32_t q = ((xh >> 10) & 0x3FFu) | 0x400u;
+  const uint32_t rbit = (xh >> 9) & 1u;
+  const uint32_t sticky = (xh & 0x1FFu) | xl;
+  q += rbit & ((sticky != 0u ? 1u : 0u) | (q & 1u));
+  uint32_t bits = q + ((uint32_t)(E + 14) << 10);
+  if (bits > 0x7BFFu) bits = 0x7BFFu;
+  return (uint16_t)(((xh >> 16) & 0x8000u) | bits);
 }
 
 }  // namespace pide
