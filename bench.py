@@ -814,7 +814,9 @@ def main():
     # ---- end to end through the C ABI from pinned host memory, copies inside the timed
     #      region: pide_solve_stream over E_BATCHES steps of B columns (each step's input
     #      copied in and its solution copied out, overlapping the neighbouring steps' solves)
-    E_BATCHES = 4
+    # 8 steps of B per call: a time sequence of 8B right-hand sides, whose first and
+    # last half-chunk copies are the only ones not hidden under a solve
+    E_BATCHES = 8
     b_host = b.cpu().pin_memory()
     in_host = torch.empty((E_BATCHES * B, n), dtype=torch.float64).pin_memory()
     for e in range(E_BATCHES):
