@@ -382,8 +382,17 @@ pide_status pide_apply_batched(const pide_handle* hs, int32_t nprob, const doubl
  * and n <= 65536, else EINVAL with a message.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) -- make that
  * first call before any stream capture.  All calls share the array: calls
- * whose work overlaps on the GPU race and must be serialised.  Results equal
- * pide_apply's up to FP32 summation order.
+ * whose work overlaps on the GPU race and must be serialised.
+ * What it computes: the refinement of pide_apply (first apply, then `sweeps`
+ * times an FP64 stencil residual and an apply-accumulate) with every
+ * right-hand side handed to the stored inverse in FP32, where pide_apply
+ * hands the tensor cores FP16, BF16 or e4m3; the e4m3 correction term of a
+ * *_FP8 store joins the applies its correction mask selects, as in pide_apply.
+ * The two therefore agree once the refinement has converged, not apply by
+ * apply (an FP64 store needs two sweeps to come back from the FP32 right-hand
+ * side to FP64 accuracy).  The product runs on the CUDA cores (FP32 sums; FP64
+ * for the FP64 store): at 198^2 unknowns one apply takes ~0.7 ms at B = 1 and
+ * ~2 ms at B = 8.
  */
 pide_status pide_apply_noalloc(pide_handle h, const double* b_dev, double* u_dev, int32_t B,
                                int32_t sweeps, void* stream);
