@@ -494,11 +494,7 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_PREP_CLUSTER    FP16 right-hand-side prep: 1 (default) = a cluster of 4 CTAs per
  *                           column holds the column in shared memory (one HBM pass; with the
  *                           correction term in the first apply it also writes the e4m3 copy of R),
- *                           up to ~56K unknowns; 0 = one CTA per column reading it twice
- *   PIDE_TUNE_GEMM_DELTA      B > 128, fixed sweep count: 1 = the last refinement apply writes its
- *                           product as FP32 to a workspace buffer (allocated on first use, B x ld
- *                           floats) and a separate pass adds it to u, instead of the GEMM
- *                           epilogue reading and rewriting u; 0 (default) = accumulate in place */
+ *                           up to ~56K unknowns; 0 = one CTA per column reading it twice */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,
@@ -518,8 +514,7 @@ typedef enum {
   PIDE_TUNE_BATCH_TC = 15,
   PIDE_TUNE_BATCH_BN = 16,
   PIDE_TUNE_BATCH_TN = 17,
-  PIDE_TUNE_PREP_CLUSTER = 18,
-  PIDE_TUNE_GEMM_DELTA = 19
+  PIDE_TUNE_PREP_CLUSTER = 18
 } pide_tune_key;
 pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value);
 pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* value);

@@ -372,7 +372,7 @@ class Solver:
                  "gemm_2cta": 10, "gemm_a_hint": 11,
                  "resid_prefetch": 12, "corr_mask": 13,
                  "gemm_u_hint": 14, "batch_tc": 15, "batch_bn": 16, "batch_tn": 17,
-                 "prep_cluster": 18, "gemm_delta": 19}
+                 "prep_cluster": 18}
 
     def set_tuning(self, **kv):
         for k, v in kv.items():

@@ -163,17 +163,6 @@ pide_status ensure_workspace(pide_ctx* c, int B) {
   return PIDE_OK;
 }
 
-// FP32 buffer for the product of a last refinement apply (gemm_delta).
-static pide_status ensure_delta(pide_ctx* c, int B) {
-  if (c->delta && B <= c->delta_B) return PIDE_OK;
-  if (c->delta) cudaFree(c->delta);
-  c->delta = nullptr;
-  c->delta_B = 0;
-  PIDE_CUDA_TRY(cudaMalloc((void**)&c->delta, (size_t)B * c->ld * sizeof(float)));
-  c->delta_B = B;
-  return PIDE_OK;
-}
-
 // ---------------------------------------------------------------- apply
 
 pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
@@ -273,17 +262,7 @@ pide_status solve_s(pide_ctx* c, const double* b, int mode, const double* lift, 
     if (hist && k < HIST_MAX) PIDE_TRY(launch_record(c, B, hist + k, tol <= 0, st));
     if (tol > 0) PIDE_TRY(launch_check(c, B, tol, st));
     if (corr_at(k + 1)) PIDE_TRY(launch_corr_rhs(c, B, st));
-    // the last apply of the solve may write its product to an FP32 buffer and
-    // add it to x in a separate pass, instead of reading x in its epilogue
-    const bool delta = c->gemm_delta && tensor && k == sweeps - 1 && !corr_at(k + 1) &&
-                       tol <= 0 && !hist && B > 128;
-    if (delta) PIDE_TRY(ensure_delta(c, B));
-    c->delta_request = delta;
-    c->delta_used = false;
-    const pide_status as = launch_apply(c, B, x, true, st);
-    c->delta_request = false;
-    PIDE_TRY(as);
-    if (c->delta_used) PIDE_TRY(launch_delta_add(c, x, B, st));
+    PIDE_TRY(launch_apply(c, B, x, true, st));
     if (corr_at(k + 1)) PIDE_TRY(launch_apply_corr(c, B, x, st));
   }
   return PIDE_OK;
@@ -569,7 +548,7 @@ extern "C" void pide_destroy(pide_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {h->sym, h->sym_lo, h->sym_scale, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
-                  h->corr, h->corr_scale, h->Rc, h->col_scale_c, h->delta,
+                  h->corr, h->corr_scale, h->Rc, h->col_scale_c,
                   h->lift, h->colmax, h->flags, h->hist, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1155,10 +1134,6 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       if (value != 0 && value != 1) break;
       h->prep_cluster = value;
       return PIDE_OK;
-    case PIDE_TUNE_GEMM_DELTA:
-      if (value != 0 && value != 1) break;
-      h->gemm_delta = value;
-      return PIDE_OK;
   }
   set_error("pide_set_tuning: unknown key or value out of range");
   return PIDE_EINVAL;
@@ -1189,7 +1164,6 @@ extern "C" pide_status pide_get_tuning(pide_handle h, int32_t key, int32_t* valu
     case PIDE_TUNE_BATCH_BN: *value = h->batch_bn; return PIDE_OK;
     case PIDE_TUNE_BATCH_TN: *value = h->batch_tn; return PIDE_OK;
     case PIDE_TUNE_PREP_CLUSTER: *value = h->prep_cluster; return PIDE_OK;
-    case PIDE_TUNE_GEMM_DELTA: *value = h->gemm_delta; return PIDE_OK;
   }
   set_error("pide_get_tuning: unknown key");
   return PIDE_EINVAL;

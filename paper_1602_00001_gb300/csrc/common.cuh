@@ -109,11 +109,6 @@ struct pide_ctx {
   int gemm_2cta = 1;                // B > 128 on SM pairs (tcgen05 cta_group::2)
   int gemm_a_hint = 1;              // L2 policy of the inverse's TMA loads (policy_for_a)
   int gemm_u_hint = 1;              // epilogue's u loads/stores: 0 plain, 1 L2 evict-first
-  int gemm_delta = 0;               // last refinement apply: product to `delta`, then u += delta
-  float* delta = nullptr;           // [delta_B][ld] FP32 product of that apply
-  int delta_B = 0;
-  bool delta_request = false;       // set around the launch that should write `delta`
-  bool delta_used = false;          // whether that launch did
   int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
   int overlap = 0;                  // residual of one column group under the GEMM of the other
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
@@ -186,8 +181,6 @@ pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st);
 // reset: zero colmax afterwards (the tolerance check does it when tol > 0).
 // Skipped once the tolerance flag marks the solve done.
 pide_status launch_record(pide_ctx* c, int B, double* slot, bool reset, cudaStream_t st);
-// u[col][p] += delta[col][p] (the FP32 product an apply wrote instead of accumulating)
-pide_status launch_delta_add(pide_ctx* c, double* u, int B, cudaStream_t st);
 constexpr int HIST_MAX = 64;
 // The refined solve of step 3 (api.cu): x = Q(L^-1) q(f), then `sweeps` sweeps
 // x += Q(L^-1) q(f - L x); hist (device, may be NULL): per-sweep residual record.
@@ -381,11 +374,6 @@ __device__ __forceinline__ double ld_f64_hint(const double* p, uint64_t policy) 
 }
 __device__ __forceinline__ void st_f64_hint(double* p, double v, uint64_t policy) {
   asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
-               : "memory");
-}
-
-__device__ __forceinline__ void st_f32_hint(float* p, float v, uint64_t policy) {
-  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy)
                : "memory");
 }
 

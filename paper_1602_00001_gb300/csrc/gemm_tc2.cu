@@ -174,8 +174,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
                 int dp_tiles, int sk, double* __restrict__ u, int accumulate,
                 const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-                uint32_t* __restrict__ flags, int a_hint, int u_hint,
-                float* __restrict__ dout, int ldd) {
+                uint32_t* __restrict__ flags, int a_hint, int u_hint) {
   constexpr bool FP8 = MODE == 1 || MODE == 2;   // kind::f8f6f4 (else kind::f16)
   constexpr bool SCALED = MODE != 0;              // epilogue applies row and column scales
   constexpr bool LO = MODE == 2;
@@ -366,19 +365,6 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           // the 32 old values first: loads issued together instead of one
           // load-add-store round trip per column
           double old[32];
-          if (dout) {
-            // the product alone, in FP32: the caller adds it to u afterwards
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int col = colbase + j;
-              if (col < B) {
-                float a = __uint_as_float(v[j]);
-                if (SCALED) a = a * rs * col_scale[col];
-                st_f32_hint(dout + (size_t)col * ldd + p, a, upol);
-              }
-            }
-            continue;
-          }
           if (accumulate && whole) {
             if (u_hint) {
 #pragma unroll
@@ -476,12 +462,9 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const CUtensorMap& R = corr ? c->tmRc : c->tmR;
   const float* rs = corr ? c->corr_scale : c->row_scale;
   const float* cs = corr ? c->col_scale_c + col0 : (MODE != 0 ? c->col_scale + col0 : nullptr);
-  // the product to the FP32 delta buffer instead of u += (whole tiles only)
-  float* dout = (c->delta_request && accumulate && !sk && c->delta) ? c->delta : nullptr;
-  c->delta_used = dout != nullptr;
   kern<<<2 * clusters, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, sk, u,
                                         accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint,
-                                        c->gemm_u_hint, dout, c->ld);
+                                c->gemm_u_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }

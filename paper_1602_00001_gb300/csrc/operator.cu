@@ -532,23 +532,6 @@ pide_status launch_check(pide_ctx* c, int B, double tol, cudaStream_t st) {
   return PIDE_OK;
 }
 
-__global__ void delta_add_kernel(double* __restrict__ u, const float* __restrict__ delta, int n,
-                                 int ld) {
-  const int col = blockIdx.y;
-  double* uc = u + (size_t)col * n;
-  const float* dc = delta + (size_t)col * ld;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
-    uc[p] += f32_to_f64(dc[p]);
-}
-
-pide_status launch_delta_add(pide_ctx* c, double* u, int B, cudaStream_t st) {
-  if (B == 0) return PIDE_OK;
-  ProfScope ps(c, st, 1);   // timed with the residuals (an elementwise pass over u)
-  delta_add_kernel<<<col_grid(c->n, B), 256, 0, st>>>(u, c->delta, c->n, c->ld);
-  PIDE_CUDA_TRY(cudaGetLastError());
-  return PIDE_OK;
-}
-
 pide_status launch_record(pide_ctx* c, int B, double* slot, bool reset, cudaStream_t st) {
   ProfScope ps(c, st, 3);
   record_kernel<<<1, 256, 0, st>>>(c->colmax, c->colmax + c->ws_B, B, slot, reset ? 1 : 0,

@@ -124,25 +124,3 @@ def test_pair_stream_k_at_full_size():
     # the same FP32 sums in another order: bounded by the contraction of |Q| |R|
     d = ((u1 - u0).abs().amax(dim=1) / u0.abs().amax(dim=1)).max().item()
     assert d < 1e-4, d
-
-
-def test_delta_out_last_apply_matches_in_place():
-    """PIDE_TUNE_GEMM_DELTA: the last refinement apply writes its product as
-    FP32 and a separate pass adds it to u; the result equals the in-place
-    accumulation up to the FP32 rounding of the correction (far below its own
-    size), and both reach the oracle."""
-    from paper_1602_00001_gb300.binding import Solver
-    nx = ny = 82
-    h = 1.0 / 81
-    eps = W.eps_fourier(nx, ny, h, seed=9)
-    b = O.rhs_from_charge(nx, ny, h, eps, W.gaussian_blobs(nx, ny, h, 3, batch=600))
-    s = Solver(nx, ny, h, eps, "fp16_fp8")
-    s.set_tuning(gemm_streamk=0)
-    u0 = s.apply(b, sweeps=1)
-    s.set_tuning(gemm_delta=1)
-    u1 = s.apply(b, sweeps=1)
-    d = float((u1 - u0).abs().max() / u0.abs().max())
-    assert 0 <= d < 1e-9, d
-    ref = O.solve(nx, ny, eps, b[[0, 599]], route="band")
-    assert O.rel_error_eq6(u1[[0, 599]].cpu().numpy(), ref) < 1e-6
-    s.close()
