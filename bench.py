@@ -44,11 +44,13 @@ WORKLOAD = "198^2 interior (200x200 nodes), Fourier-field eps, 16 moving charges
 # one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the SM-pair
 # GEMM launches of a timed step); valid only for the kernel source it was taken on
 # (sha1 of csrc/gemm_tc2.cu + csrc/common.cuh), and reported as a stored figure.
-# Average over the FP16 launches of a step (first apply 5.69 GB, the refinement
-# apply 8.51 GB); the e4m3 correction GEMM (2.91 GB) is reported on its own.
-GEMM_TRAFFIC = {"sha1": "9e0a111ab3c4b31aceb2ff4c7fcfb63b402bc6d4", "bytes": 7.10e9,
+# Average over the FP16 launches of two timed steps (first apply 4.8-5.5 GB, the
+# refinement apply 7.7-7.9 GB); the e4m3 correction GEMM (2.70 GB) is reported on its own.
+GEMM_TRAFFIC = {"sha1": "9553bcda0851555bfa96da3a7c5aeed393fb0b60", "bytes": 6.49e9,
                 "precision": "fp16_fp8", "batch": 1024, "nodes": 200, "sweeps": 1,
-                "corr_mask": 1, "corr_bytes": 2.91e9}
+                "corr_mask": 1, "corr_bytes": 2.70e9,
+                "source": "stored ncu capture of this kernel source (dram__bytes_read.sum + "
+                          "dram__bytes_write.sum, one pass, NVTX-selected timed steps)"}
 
 
 def gemm_source_sha1():
@@ -927,6 +929,7 @@ def main():
                   "auto": auto_rep},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": traffic,
+                     "traffic_source": GEMM_TRAFFIC["source"] if traffic else None,
                      "kernel": (f"gemm_tc2_kernel (tcgen05 cta_group::2 {args.precision}, M=256 N=256 per SM pair)"
                                 if s.get_tuning()["gemm_2cta"] and B > 128 else
                                 f"gemm_tc_kernel (tcgen05 {args.precision}, M=128 N=256)"),
