@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df_arith.cuh"
 
 namespace pide {
 namespace {
@@ -30,6 +31,8 @@ namespace {
 struct BatchProb {
   const void* inv;      // [n][ld] FP32 or BF16 stored inverse
   const double* w;      // [4][n] Eq. (3) weights
+  const float4* wsp;    // [2][n] the weights split into float pairs (hi, then lo), zero
+                        // toward boundary neighbours
   const double* b;      // [B][n]
   double* u;            // [B][n]
   float* R;             // [B][ld] FP32 right-hand side / residual
@@ -309,7 +312,13 @@ __global__ void __launch_bounds__(256) batched_apply_kernel(const BatchProb* __r
   }
 }
 
-// Prep (residual == 0): R = float(b).  Residual: R = float(b - L u), FP64.
+// Prep (residual == 0): R = q(b).  Residual: R = q(b - L u), the Eq. (3)
+// stencil in double-float arithmetic on the integer and FP32 pipes (each FP64
+// input split into two floats, error-free products and sums: absolute error
+// ~2^-45 (|u_p| + sum_q w_pq |u_q|)); nodes with inputs outside the split's
+// range, or whose own scale max(|b_p|, |u_p|) is below 2^-60, take the FP64
+// formula.  q: FP32 (rounded from the pair) or BF16 (rounded to nearest from the
+// pair, or from b's FP64 bits in the prep).
 __global__ void __launch_bounds__(256) batched_vec_kernel(const BatchProb* __restrict__ probs,
                                                           const int2* __restrict__ items,
                                                           int residual, int phase) {
@@ -320,19 +329,48 @@ __global__ void __launch_bounds__(256) batched_vec_kernel(const BatchProb* __res
   const double* bc = P.b + (size_t)col * P.n;
   const double* uc = P.u + (size_t)col * P.n;
   float* Rc = P.R + (size_t)col * P.ld;
+  __nv_bfloat16* Rb = reinterpret_cast<__nv_bfloat16*>(P.R) + (size_t)col * P.ld;
   const int n = P.n, mx = P.mx;
+  const float4* wh4 = P.wsp;
+  const float4* wl4 = P.wsp + n;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    double r = bc[p];
-    if (residual) {
-      const int c = p % mx;
-      r -= uc[p];
-      if (c > 0) r = fma(P.w[p], uc[p - 1], r);
-      if (c < mx - 1) r = fma(P.w[n + p], uc[p + 1], r);
-      if (p >= mx) r = fma(P.w[2 * n + p], uc[p - mx], r);
-      if (p + mx < n) r = fma(P.w[3 * n + p], uc[p + mx], r);
+    if (!residual) {
+      const double bp = bc[p];
+      if (P.rbf16) {
+        Rb[p] = bf16_of_f64(bp);
+      } else {
+        float bh, bl;
+        const uint32_t e = split47<false>(bp, bh, bl);
+        Rc[p] = (e <= E_SPLIT_MAX && (e >= 920u || is_zero(bp))) ? __fadd_rn(bh, bl)
+                                                                   : __double2float_rn(bp);
+      }
+      continue;
     }
-    if (P.rbf16) reinterpret_cast<__nv_bfloat16*>(P.R)[(size_t)col * P.ld + p] = __double2bfloat16(r);
-    else Rc[p] = (float)r;
+    // neighbours from clamped indices: the split weights toward boundary nodes are zero
+    const double vw = uc[p > 0 ? p - 1 : 0], ve = uc[p + 1 < n ? p + 1 : n - 1];
+    const double vs = uc[p >= mx ? p - mx : 0], vn = uc[p + mx < n ? p + mx : n - 1];
+    const double vp = uc[p], bp = bc[p];
+    float wh_, wl_, eh, el, sh_, sl_, nh, nl, ph, pl, bh, bl;
+    const uint32_t ew = split47<false>(vw, wh_, wl_), ee = split47<false>(ve, eh, el);
+    const uint32_t es = split47<false>(vs, sh_, sl_), en = split47<false>(vn, nh, nl);
+    const uint32_t ep = split47<false>(vp, ph, pl), eb = split47<false>(bp, bh, bl);
+    const uint32_t emax = max(max(max(ew, ee), max(es, en)), max(ep, eb));
+    float s, e;
+    if (emax <= E_SPLIT_MAX && max(ep, eb) >= E_NODE_MIN) {
+      const float4 wh = wh4[p], wl = wl4[p];
+      float ah = bh, al = bl;
+      df_add(ah, al, -ph, -pl);
+      df_fma(ah, al, wh.x, wl.x, wh_, wl_);
+      df_fma(ah, al, wh.y, wl.y, eh, el);
+      df_fma(ah, al, wh.z, wl.z, sh_, sl_);
+      df_fma(ah, al, wh.w, wl.w, nh, nl);
+      s = __fadd_rn(ah, al);
+      e = __fsub_rn(al, __fsub_rn(s, ah));
+    } else {
+      split_f64_slow(residual_node_fp64(bc, uc, P.w, nullptr, n, mx, n, p), s, e);
+    }
+    if (P.rbf16) Rb[p] = bf16_of_pair(s, e);
+    else Rc[p] = s;
   }
 }
 
@@ -648,7 +686,7 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
       batch_free(p);
       return s;
     }
-    probs[k] = BatchProb{h->inv, h->w, b[k], u[k], (float*)h->R, h->ld, h->n, h->mx, Bs[k],
+    probs[k] = BatchProb{h->inv, h->w, h->wsp, b[k], u[k], (float*)h->R, h->ld, h->n, h->mx, Bs[k],
                          h->prec == PIDE_FP32 ? 0 : 1,
                          sweeps_k ? (sweeps_k[k] < 0 ? 0 : sweeps_k[k]) : 1 << 30, 0};
     const bool tc_bf16 = h->prec == PIDE_BF16 && h->tmA_ok;
