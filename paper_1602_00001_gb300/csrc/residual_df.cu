@@ -217,8 +217,8 @@ __device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float wh, float 
 // on zeros and not stored.  The fast route needs max(|f_p|, |u_p|) >= 2^-60
 // and a finite result (a value at or above 2^128 is staged as NaN); other
 // nodes take the FP64 route.
-template <int RF, int SM_NR, bool DIM3>
-__global__ void __launch_bounds__(256) residual_df_kernel(
+template <int RF, int SM_NR, bool DIM3, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) residual_df_kernel(
     const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int plane, int B,
     int ldr, const float4* __restrict__ wh4, const float4* __restrict__ wl4,
     const float4* __restrict__ wz4, const double* __restrict__ w4,
@@ -429,7 +429,9 @@ static pide_status launch_df_smem(pide_ctx* c, const double* b, const double* u,
       break;
     }
     case RF_F16: {
-      auto k = residual_df_kernel<RF_F16, NR, DIM3>;
+      // resid_shape 4: eight nodes per thread, registers capped for five blocks per SM
+      auto k = (NR == 8 && !DIM3 && c->resid_shape == 4) ? residual_df_kernel<RF_F16, NR, DIM3, 5>
+                                                          : residual_df_kernel<RF_F16, NR, DIM3>;
       if (smem > 48 * 1024)
         PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
@@ -458,7 +460,7 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   // default (-1): 8 nodes per thread (16 in 3-D stages relatively less halo
   // but measured slower at 32^3: 1.05 against 0.85 ms per step, 98 KB of
   // shared memory per block leaves two blocks per SM)
-  const int nr = c->resid_shape < 0 ? 8 : SM_NRS[c->resid_shape & 3];
+  const int nr = (c->resid_shape < 0 || c->resid_shape == 4) ? 8 : SM_NRS[c->resid_shape & 3];
   const size_t halo = three ? (size_t)plane_of(c) : (size_t)c->mx;
   const size_t smem = (256 * (size_t)nr + 2 * halo + 2) * sizeof(float4);
   if (three) {
