@@ -465,9 +465,11 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           on pairs of SMs (tcgen05 cta_group::2, 256 x 256 tiles, each SM
  *                           staging half of each operand tile); 0: one SM per 128 x 256 tile
  *   PIDE_TUNE_GEMM_A_HINT   L2 policy of the tensor-core apply's loads of the stored inverse:
- *                           0 evict-first, 1 (default) evict-normal, 2 evict-last (measured
+ *                           0 evict-first, 1 evict-normal, 2 (default) evict-last (measured
  *                           on the SM-pair kernel at 198^2, B = 1024: 6.9 GB of DRAM reads per
- *                           launch with evict-first, 4.8 GB with either other policy, same time)
+ *                           launch with evict-first, 4.8 GB with either other policy; the
+ *                           refined step 2 % shorter with evict-last than evict-normal, three
+ *                           alternating runs each on one box)
  *   PIDE_TUNE_RESID_PREFETCH  the refinement residual's L2 prefetch distance, in column pairs:
  *                           each block prefetches its tile of the pair that many pairs ahead
  *                           (0 = none, up to 4096; default 4: the 2-D residual at 158^2 and

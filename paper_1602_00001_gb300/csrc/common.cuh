@@ -107,7 +107,7 @@ struct pide_ctx {
   int gemm_bn_large = 256;          // BN for B > 128: 128 or 256
   int gemm_streamk = 1;             // stream-K tail after the full data-parallel waves
   int gemm_2cta = 1;                // B > 128 on SM pairs (tcgen05 cta_group::2)
-  int gemm_a_hint = 1;              // L2 policy of the inverse's TMA loads (policy_for_a)
+  int gemm_a_hint = 2;              // L2 policy of the inverse's TMA loads (policy_for_a)
   int gemm_u_hint = 1;              // epilogue's u loads/stores: 0 plain, 1 L2 evict-first
   int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
   int overlap = 0;                  // residual of one column group under the GEMM of the other
