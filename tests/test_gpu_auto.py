@@ -137,3 +137,22 @@ def test_sweeps_auto_needs_an_auto_handle():
     with pytest.raises(PideError):
         s.auto_report()
     s.close()
+
+
+def test_auto_3d():
+    """PIDE_AUTO on a 3-D grid (pide_setup_3d): the chosen store with its
+    measured sweep count reaches the 3-D oracle to 1e-6."""
+    from oracle import pide_oracle3d as O3
+    from paper_1602_00001_gb300.binding import SWEEPS_AUTO, Solver3D
+    nx, ny, nz = 14, 13, 12
+    rng = np.random.default_rng(8)
+    eps = np.exp(0.5 * rng.standard_normal((nz, ny, nx)))
+    n = (nx - 2) * (ny - 2) * (nz - 2)
+    b = rng.standard_normal((40, n))
+    s = Solver3D(nx, ny, nz, 1.0 / (nx - 1), eps, "auto")
+    rep = s.auto_report()
+    assert s.precision == rep["chosen"] and rep["sweeps"] >= 0
+    u = s.apply(b, sweeps=SWEEPS_AUTO).cpu().numpy()
+    ref = O3.solve(nx, ny, nz, eps, b[[0, 39]], route="band")
+    assert np.max(np.abs(u[[0, 39]] - ref)) / np.max(np.abs(ref)) < 1e-6
+    s.close()
