@@ -217,8 +217,8 @@ __device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float wh, float 
 // on zeros and not stored.  The fast route needs max(|f_p|, |u_p|) >= 2^-60
 // and a finite result (a value at or above 2^128 is staged as NaN); other
 // nodes take the FP64 route.
-template <int RF, int SM_NR, bool DIM3, int MINB = 1>
-__global__ void __launch_bounds__(256, MINB) residual_df_kernel(
+template <int RF, int SM_NR, bool DIM3>
+__device__ __forceinline__ void residual_df_tile(
     const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int plane, int B,
     int ldr, const float4* __restrict__ wh4, const float4* __restrict__ wl4,
     const float4* __restrict__ wz4, const double* __restrict__ w4,
@@ -341,6 +341,27 @@ __global__ void __launch_bounds__(256, MINB) residual_df_kernel(
   }
 }
 
+#define RESIDUAL_DF_ARGS                                                                       \
+  const double* __restrict__ b, const double* __restrict__ u, int n, int mx, int plane, int B,  \
+      int ldr, const float4* __restrict__ wh4, const float4* __restrict__ wl4,                  \
+      const float4* __restrict__ wz4, const double* __restrict__ w4,                            \
+      const double* __restrict__ lift, void* __restrict__ R, const float* __restrict__ col_scale, \
+      double* __restrict__ colmax_r, int track, const uint32_t* __restrict__ flags, int pf
+
+// The kernel with the compiler's register choice, and the same with registers
+// capped so that five blocks fit an SM (PIDE_TUNE_RESID_SHAPE = 4).
+template <int RF, int SM_NR, bool DIM3>
+__global__ void __launch_bounds__(256) residual_df_kernel(RESIDUAL_DF_ARGS) {
+  residual_df_tile<RF, SM_NR, DIM3>(b, u, n, mx, plane, B, ldr, wh4, wl4, wz4, w4, lift, R,
+                                    col_scale, colmax_r, track, flags, pf);
+}
+template <int RF, int SM_NR, bool DIM3>
+__global__ void __launch_bounds__(256, 5) residual_df_kernel_occ5(RESIDUAL_DF_ARGS) {
+  residual_df_tile<RF, SM_NR, DIM3>(b, u, n, mx, plane, B, ldr, wh4, wl4, wz4, w4, lift, R,
+                                    col_scale, colmax_r, track, flags, pf);
+}
+#undef RESIDUAL_DF_ARGS
+
 // Prep for BF16 right-hand sides, forward mode: R = bf16(b + lift) rounded to
 // nearest (integer rounding of b alone; with a lift, from the exact pair of
 // the sticky split); optionally max |f| per column.
@@ -430,7 +451,7 @@ static pide_status launch_df_smem(pide_ctx* c, const double* b, const double* u,
     }
     case RF_F16: {
       // resid_shape 4: eight nodes per thread, registers capped for five blocks per SM
-      auto k = (NR == 8 && !DIM3 && c->resid_shape == 4) ? residual_df_kernel<RF_F16, NR, DIM3, 5>
+      auto k = (NR == 8 && !DIM3 && c->resid_shape == 4) ? residual_df_kernel_occ5<RF_F16, NR, DIM3>
                                                           : residual_df_kernel<RF_F16, NR, DIM3>;
       if (smem > 48 * 1024)
         PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
