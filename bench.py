@@ -513,9 +513,10 @@ def threed_workload(args):
                        "setup_ms_bf16": s.info().setup_ms},
             "accuracy": {"max_rel_err_eq6_vs_fp64": err, "target": 1e-6, "err_by_sweeps": errs},
             "kernel_ms_per_step": {c: prof[c][1] / (args.steps + 1) for c in prof},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops_sustained"],
-                         "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops_sustained"],
-                         "traffic": None, "peak_source": f"{pk_kind} bf16_tflops_sustained"}}
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
+                         "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],
+                         "traffic": None, "peak_source": f"{pk_kind} bf16_tflops (burst)"}}
     print(json.dumps(line))
     return 0
 
@@ -857,14 +858,19 @@ def main():
     terms = 2 if args.precision == "fp8x2" else 1
     flops_total = 2.0 * n * n * B * (1 + k) * args.steps * terms
     achieved = flops_total / (apply_ms * 1e-3) / 1e12
+    # The GEMM launches (~1.9 ms each) are timed inside a 5 ms step and a timed region
+    # of a fraction of a second: the burst figure is the denominator; the fraction of
+    # the seconds-long sustained figure (power-capped) is reported beside it.
     if args.precision == "fp8x2":
-        peak_tf = pk["bf16_tflops_sustained"] * 2.0       # nominal FP8:BF16 dense ratio 4.5:2.25
-        peak_src = f"{pk_kind} bf16_tflops_sustained x 2 (nominal FP8/BF16 ratio)"
+        ratio = 2.0                                        # nominal FP8:BF16 dense ratio 4.5:2.25
+        peak_src = f"{pk_kind} bf16_tflops (burst) x 2 (nominal FP8/BF16 ratio)"
     else:
-        peak_tf = pk["bf16_tflops_sustained"]
-        peak_src = f"{pk_kind} bf16_tflops_sustained"
+        ratio = 1.0
+        peak_src = f"{pk_kind} bf16_tflops (burst)"
         if args.precision.startswith("fp16"):
             peak_src += " (FP16 and BF16 share the dense tensor rate: nominal ratio 1)"
+    peak_tf = pk["bf16_tflops"] * ratio
+    sustained_tf = pk["bf16_tflops_sustained"] * ratio
     traffic = None
     tn = s.get_tuning()
     traffic_valid = (gemm_source_sha1() == GEMM_TRAFFIC["sha1"]
@@ -880,11 +886,12 @@ def main():
     if args.precision.endswith("_fp8") and prof["other"][0] > 0:
         c_launches, c_ms = prof["other"]
         c_tf = 2.0 * n * n * B * c_launches / (c_ms * 1e-3) / 1e12
-        c_peak = pk["bf16_tflops_sustained"] * 2.0
+        c_peak = pk["bf16_tflops"] * 2.0
         corr_line = {"kernel": "gemm_tc2_kernel (tcgen05 cta_group::2 e4m3 correction term)",
                      "launches": c_launches, "avg_launch_ms": c_ms / c_launches,
                      "achieved": c_tf, "peak": c_peak, "unit": "TFLOP/s", "frac": c_tf / c_peak,
-                     "peak_source": f"{pk_kind} bf16_tflops_sustained x 2 (nominal FP8/BF16 ratio)",
+                     "frac_of_sustained": c_tf / (pk["bf16_tflops_sustained"] * 2.0),
+                     "peak_source": f"{pk_kind} bf16_tflops (burst) x 2 (nominal FP8/BF16 ratio)",
                      "corr_mask": s.get_tuning()["corr_mask"],
                      "traffic": GEMM_TRAFFIC["corr_bytes"] if traffic_valid else None}
 
@@ -928,7 +935,8 @@ def main():
                   "chosen_by": "pide_setup_auto (measured contraction)" if auto_rep else "--precision",
                   "auto": auto_rep},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": traffic,
+                     "frac": achieved / peak_tf, "frac_of_sustained": achieved / sustained_tf,
+                     "traffic": traffic,
                      "traffic_source": GEMM_TRAFFIC["source"] if traffic else None,
                      "kernel": (f"gemm_tc2_kernel (tcgen05 cta_group::2 {args.precision}, M=256 N=256 per SM pair)"
                                 if s.get_tuning()["gemm_2cta"] and B > 128 else
