@@ -459,8 +459,7 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           of pide_info are always FP64.
  *   PIDE_TUNE_RESID_SHAPE   launch shape of that residual kernel: nodes per thread (a tile of
  *                           256 x that many nodes per block, two columns per block):
- *                           -1 (default): 8; 0: 4, 1: 8, 2: 2, 3: 16; 4: 8 with registers capped
- *                           for five blocks per SM (FP16 residuals of 2-D grids)
+ *                           -1 (default): 8; 0: 4, 1: 8, 2: 2, 3: 16
  *   PIDE_TUNE_GEMM_2CTA     1 (default): for B > 128 (with GEMM_BN 256) the tensor-core apply runs
  *                           on pairs of SMs (tcgen05 cta_group::2, 256 x 256 tiles, each SM
  *                           staging half of each operand tile); 0: one SM per 128 x 256 tile

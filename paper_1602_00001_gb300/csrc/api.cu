@@ -1095,7 +1095,7 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       h->resid_emul = value;
       return PIDE_OK;
     case PIDE_TUNE_RESID_SHAPE:
-      if (value < -1 || value > 4) break;
+      if (value < -1 || value > 3) break;
       h->resid_shape = value;
       return PIDE_OK;
     case PIDE_TUNE_GEMM_2CTA:

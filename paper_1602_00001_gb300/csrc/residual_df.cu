@@ -348,15 +348,8 @@ __device__ __forceinline__ void residual_df_tile(
       const double* __restrict__ lift, void* __restrict__ R, const float* __restrict__ col_scale, \
       double* __restrict__ colmax_r, int track, const uint32_t* __restrict__ flags, int pf
 
-// The kernel with the compiler's register choice, and the same with registers
-// capped so that five blocks fit an SM (PIDE_TUNE_RESID_SHAPE = 4).
 template <int RF, int SM_NR, bool DIM3>
 __global__ void __launch_bounds__(256) residual_df_kernel(RESIDUAL_DF_ARGS) {
-  residual_df_tile<RF, SM_NR, DIM3>(b, u, n, mx, plane, B, ldr, wh4, wl4, wz4, w4, lift, R,
-                                    col_scale, colmax_r, track, flags, pf);
-}
-template <int RF, int SM_NR, bool DIM3>
-__global__ void __launch_bounds__(256, 5) residual_df_kernel_occ5(RESIDUAL_DF_ARGS) {
   residual_df_tile<RF, SM_NR, DIM3>(b, u, n, mx, plane, B, ldr, wh4, wl4, wz4, w4, lift, R,
                                     col_scale, colmax_r, track, flags, pf);
 }
@@ -450,9 +443,7 @@ static pide_status launch_df_smem(pide_ctx* c, const double* b, const double* u,
       break;
     }
     case RF_F16: {
-      // resid_shape 4: eight nodes per thread, registers capped for five blocks per SM
-      auto k = (NR == 8 && !DIM3 && c->resid_shape == 4) ? residual_df_kernel_occ5<RF_F16, NR, DIM3>
-                                                          : residual_df_kernel<RF_F16, NR, DIM3>;
+      auto k = residual_df_kernel<RF_F16, NR, DIM3>;
       if (smem > 48 * 1024)
         PIDE_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k<<<g, 256, smem, st>>>(b, u, c->n, c->mx, plane, B, ldr, wh, wl, wz, c->w, lift, R, col_scale, colmax_r, t, flags, c->resid_prefetch);
@@ -481,7 +472,7 @@ pide_status launch_residual_df(pide_ctx* c, const double* b, const double* u, in
   // default (-1): 8 nodes per thread (16 in 3-D stages relatively less halo
   // but measured slower at 32^3: 1.05 against 0.85 ms per step, 98 KB of
   // shared memory per block leaves two blocks per SM)
-  const int nr = (c->resid_shape < 0 || c->resid_shape == 4) ? 8 : SM_NRS[c->resid_shape & 3];
+  const int nr = c->resid_shape < 0 ? 8 : SM_NRS[c->resid_shape & 3];
   const size_t halo = three ? (size_t)plane_of(c) : (size_t)c->mx;
   const size_t smem = (256 * (size_t)nr + 2 * halo + 2) * sizeof(float4);
   if (three) {

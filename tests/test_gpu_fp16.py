@@ -232,18 +232,3 @@ def test_cluster_prep_equals_one_cta_prep(prec, nx, ny, B):
     assert torch.equal(outs[1][0], outs[0][0]) and torch.equal(outs[1][1], outs[0][1])
     s.close()
 
-
-def test_residual_shape_with_five_blocks_is_bit_identical():
-    """PIDE_TUNE_RESID_SHAPE = 4 (the FP16 residual with registers capped for
-    five blocks per SM) changes the launch, not a bit of the refined result."""
-    nx = ny = 90
-    h = 1.0 / 89
-    eps = W.eps_lognormal(nx, ny, seed=41)
-    b = _b(nx, ny, h, eps, 300, seed=42)
-    s = _solver(nx, ny, h, eps, "fp16_fp8")
-    s.set_tuning(gemm_streamk=0)
-    u0 = s.apply(b, sweeps=2)
-    s.set_tuning(resid_shape=4)
-    u1 = s.apply(b, sweeps=2)
-    assert torch.equal(u0, u1)
-    s.close()
