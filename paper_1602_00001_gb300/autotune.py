@@ -166,8 +166,18 @@ def apply_cached(solver, B: int, cache: TuneCache | None = None, gpu: str | None
 # tiles (FP32 products, width 16, 32, 64) instead of the tensor cores.
 
 
+def bucket_b_batch(B: int) -> str:
+    """Column-count bucket of the batched-plan knobs: one per column-tile width
+    that covers B in one tile (a problem with 33..64 columns needs two 32-wide
+    tiles, each streaming the inverse again), so a finer split than bucket_b."""
+    for top in (8, 16, 32, 64, 128):
+        if B <= top:
+            return f"B<={top}"
+    return "B>128"
+
+
 def batch_key_for(n: int, B: int, precision: str) -> str:
-    return f"batch|{precision}|{bucket_n(n)}|{bucket_b(B)}"
+    return f"batch|{precision}|{bucket_n(n)}|{bucket_b_batch(B)}"
 
 
 def batch_candidates(precision: str, B: int):

@@ -103,6 +103,8 @@ def test_tune_batch_caches_and_applies(tmp_path):
     best, ms = T.tune_batch(s, FakeB(100), None, cache=T.TuneCache(path), gpu="GB300", timer=timer)
     assert best == {"batch_tc": 1, "batch_bn": 128} and ms == 1.0
     assert json.load(open(path))["GB300"]["batch|fp32|n<=65536|B<=128"]["knobs"] == best
+    assert T.batch_key_for(1000, 40, "bf16") == "batch|bf16|n<=1024|B<=64"
+    assert T.batch_key_for(1000, 32, "bf16") == "batch|bf16|n<=1024|B<=32"
     s2 = FakeSolver()
     s2.precision = "fp32"
     assert T.apply_cached_batch(s2, 100, cache=T.TuneCache(path), gpu="GB300")
