@@ -489,8 +489,8 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           FP64 residual refining the result; 0 = the FP32 SIMT tiles (FP32
  *                           products)
  *   PIDE_TUNE_BATCH_BN        grouped tensor-core launch: column-tile width 32, 64 or 128
- *                           (0 = default 64); each width present in a plan is one launch per
- *                           phase
+ *                           (0 = default: the narrowest that covers the problem's B in one
+ *                           tile); each width present in a plan is one launch per phase
  *   PIDE_TUNE_BATCH_TN        SIMT tiles: width 16, 32 or 64 columns (0 = default: the narrowest
  *                           covering the problem's B)
  *   PIDE_TUNE_PREP_CLUSTER    FP16 right-hand-side prep: 1 (default) = a cluster of 4 CTAs per

@@ -397,7 +397,6 @@ struct alignas(64) GroupProb {
 };
 
 constexpr int G_A_BYTES = 128 * 128;
-constexpr int GBN_DEFAULT = 64;
 // stages of the grouped kernel for a column-tile width (~160-192 KB of shared memory)
 constexpr int g_stages(int bn) { return bn >= 128 ? 6 : 8; }
 constexpr size_t g_smem(int bn) {
@@ -693,8 +692,9 @@ extern "C" pide_status pide_batch_create(const pide_handle* hs, int32_t nprob,
     const bool tc_tf32 = h->prec == PIDE_FP32 && h->batch_tc;
     if ((tc_bf16 || tc_tf32) && Bs[k] > 0) {
       // tensor cores: (problem, 128-row tile, BN-column tile) items with this problem's
-      // maps; BN from the problem's knob (0: 64)
-      const int bn = h->batch_bn > 0 ? h->batch_bn : GBN_DEFAULT;
+      // maps; BN from the problem's knob, else the narrowest width that covers its
+      // columns in one tile (each further column tile streams the inverse again)
+      const int bn = h->batch_bn > 0 ? h->batch_bn : (Bs[k] <= 32 ? 32 : (Bs[k] <= 64 ? 64 : 128));
       const int bcode = bn == 32 ? 0 : (bn == 64 ? 1 : 2);
       GroupProb g;
       std::memset(&g, 0, sizeof(g));

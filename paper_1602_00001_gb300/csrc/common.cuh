@@ -133,7 +133,7 @@ struct pide_ctx {
   int prep_cluster = 1;             // FP16 prep: one CTA cluster per column, one HBM pass
   // batched plans (pide_batch_create reads them per problem; the autotuner sets them)
   int batch_tc = 1;                 // FP32 store: 1 TF32 tensor cores, 0 FP32 SIMT tiles
-  int batch_bn = 0;                 // tensor-core column tile 32, 64 or 128 (0: 64)
+  int batch_bn = 0;                 // tensor-core column tile 32, 64 or 128 (0: the narrowest covering B)
   int batch_tn = 0;                 // SIMT tile width 16, 32 or 64 (0: the narrowest covering B)
   // refinement history of a pide_apply that fills pide_info: the worst-column
   // relative residual after apply k (k < HIST_MAX), and events timing the call

@@ -124,13 +124,13 @@ def test_tuned_cache_entry_changes_the_plan_shape(tmp_path):
     b = torch.from_numpy(W.random_interior(n, n, 2, batch=20)).cuda()
     u = torch.empty_like(b)
     plain = BatchPlan([s], [b], [u])
-    assert plain.info()["tc_items_bn"] == {32: 0, 64: 12, 128: 0}
+    assert plain.info()["tc_items_bn"] == {32: 12, 64: 0, 128: 0}      # the narrowest covering B
     plain.close()
     cache = T.TuneCache(str(tmp_path / "t.json"))
     gpu = torch.cuda.get_device_name(0)
-    cache.put(gpu, T.batch_key_for(s.n, 20, "fp32"), {"batch_tc": 1, "batch_bn": 32}, 0.1)
+    cache.put(gpu, T.batch_key_for(s.n, 20, "fp32"), {"batch_tc": 1, "batch_bn": 128}, 0.1)
     tuned = BatchPlan([s], [b], [u], tune_cache=cache)
-    assert tuned.info()["tc_items_bn"] == {32: 12, 64: 0, 128: 0}
+    assert tuned.info()["tc_items_bn"] == {32: 0, 64: 0, 128: 12}
     tuned.close()
     # a real tuning pass picks one of the candidates and leaves it on the solver
     best, ms = T.tune_batch(s, b, u, sweeps=2, cache=cache, save=False)
