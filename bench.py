@@ -382,17 +382,27 @@ def batched_workload(args):
 
 
 def batched_roofline(solvers, bs, caps, ms):
-    """HBM view of a batched step: every apply streams each problem's stored
-    inverse once (BF16 2 B, FP32 4 B per entry); 1 + cap applies per problem."""
+    """HBM view of a batched step.  Per problem (n unknowns, B columns, store
+    entries of e = 2 (BF16) or 4 (FP32) bytes) and per phase it runs (1 + cap):
+    the stored inverse n^2 e, the right-hand side R (n B e: written by the vector
+    pass, read by the apply), u (8 n B written by the first apply, read and
+    written by each later one), b (8 n B read by every vector pass) and u again
+    (8 n B read by each residual).  The fraction is taken on all of it; the
+    inverse bytes alone are reported beside it."""
     pk, kind = peaks()
-    byts = 0.0
+    inv, total = 0.0, 0.0
     for sv, b, cap in zip(solvers, bs, caps):
         esz = 4 if sv.precision == "fp32" else 2
-        byts += (1 + cap) * sv.n * sv.n * esz
-    gbs = byts / (ms * 1e-3) / 1e9
+        n, B, ph = sv.n, b.shape[0], 1 + cap
+        inv += ph * n * n * esz
+        total += ph * (n * n * esz + 2 * n * B * esz + 8 * n * B) + cap * (16 + 8) * n * B
+        total += 8 * n * B                            # the first vector pass's read of b
+    gbs = total / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": gbs / pk["hbm_gbs"], "traffic": None,
-            "note": "algorithmic inverse bytes over all applies of the step; FP32 problems run "
+            "algorithmic_bytes_per_step": total, "inverse_bytes_per_step": inv,
+            "inverse_only_frac": inv / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "note": "all algorithmic bytes of the step (inverse, R, u, b); FP32 problems run "
                     "on the TF32 tensor cores unless their knob keeps the SIMT tiles"}
 
 
