@@ -155,11 +155,13 @@ typedef struct {
 
 /* Per-kernel-class event timing, recorded on the launching stream. */
 typedef struct {
-  int32_t launches[4];   /* [0] apply (GEMM/GEMV) [1] residual [2] rhs prep (with the
+  int32_t launches[5];   /* [0] apply (GEMM/GEMV) [1] residual [2] rhs prep (with the
                             e4m3 copy of R for the correction term) [3] other: the
                             correction term's FP8 GEMM, the tolerance check, the
-                            adjoint's face gradients */
-  double ms[4];          /* summed CUDA-event time per class */
+                            adjoint's face gradients [4] reduce: the sums of the
+                            K-split last round of a tensor-core apply on SM pairs
+                            (PIDE_TUNE_GEMM_STREAMK) */
+  double ms[5];          /* summed CUDA-event time per class */
 } pide_profile;
 
 /*
@@ -434,8 +436,13 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_GEMV_MAX_B    largest B served by the GEMV instead of the GEMM: 1..8 (default 1)
  *   PIDE_TUNE_GEMM_BN       tensor-core tile width for B > 128: 128 or 256 (default 256)
  *   PIDE_TUNE_GEMM_STREAMK  1 (default): split the last partial wave of tiles over all SMs by
- *                           k-blocks (FP64 atomic partial sums) -- on SM pairs only when
- *                           there are fewer than four full waves; 0: whole tiles only
+ *                           k-blocks.  Single SMs (B <= 128 or GEMM_BN 128): FP64 atomic
+ *                           partial sums.  SM pairs: when the last round holds at most
+ *                           half as many tiles as there are pairs, each of its tiles is
+ *                           cut into P = pairs / tiles K-ranges (at least 8 k-blocks each),
+ *                           the pieces write FP32 partial tiles to a handle-owned buffer
+ *                           and a reduction kernel adds them to u in FP64, in piece
+ *                           order (deterministic); 0: whole tiles only
  *   PIDE_TUNE_OVERLAP       1: for B >= 512 with tol <= 0, split the columns in
  *                           two groups and run each group's FP64 residual on a
  *                           low-priority internal stream under the other group's

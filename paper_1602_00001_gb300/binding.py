@@ -64,7 +64,7 @@ class BatchInfo(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int32 * 4), ("ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_int32 * 5), ("ms", ctypes.c_double * 5)]
 
 
 class PideError(RuntimeError):
@@ -437,7 +437,8 @@ class Solver:
     @contextmanager
     def profile(self):
         """Event-time every kernel launched inside the block; yields a dict
-        filled at exit: {'apply': (launches, ms), 'residual': ..., 'prep': ..., 'other': ...}."""
+        filled at exit: {'apply': (launches, ms), 'residual': ..., 'prep': ..., 'other': ...,
+        'reduce': ...} ('reduce': the sums of a tensor-core apply's K-split last round)."""
         out: dict = {}
         _check(self.lib.pide_profile_begin(self.handle), "pide_profile_begin")
         try:
@@ -445,7 +446,7 @@ class Solver:
         finally:
             p = Profile()
             _check(self.lib.pide_profile_end(self.handle, ctypes.byref(p)), "pide_profile_end")
-            for i, name in enumerate(["apply", "residual", "prep", "other"]):
+            for i, name in enumerate(["apply", "residual", "prep", "other", "reduce"]):
                 out[name] = (int(p.launches[i]), float(p.ms[i]))
 
 

@@ -132,6 +132,14 @@ pide_status make_tma_rhs_corr(pide_ctx* c, int bn) {
 // ---------------------------------------------------------------- workspace
 
 pide_status ensure_workspace(pide_ctx* c, int B) {
+  // the SM-pair GEMM's partial tiles: one 256 x 256 FP32 slot per pair (20 MB
+  // at 152 SMs), allocated once so that a captured apply allocates nothing
+  if (!c->tail_ws && (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2 ||
+                      c->prec == PIDE_FP16)) {
+    const int slots = c->num_sms / 2 > 0 ? c->num_sms / 2 : 1;
+    PIDE_CUDA_TRY(cudaMalloc((void**)&c->tail_ws, (size_t)slots * 256 * 256 * sizeof(float)));
+    c->tail_slots = slots;
+  }
   if (B <= c->ws_B && c->R) return PIDE_OK;
   int nb = B < 16 ? 16 : B;
   if (c->R) cudaFree(c->R);
@@ -165,15 +173,26 @@ pide_status ensure_workspace(pide_ctx* c, int B) {
 
 // ---------------------------------------------------------------- apply
 
-pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
-                         int col0) {
-  if (B == 0) return PIDE_OK;
+static pide_status apply_dispatch(pide_ctx* c, int B, double* u, bool accumulate,
+                                  cudaStream_t st, int col0) {
   ProfScope ps(c, st, 0);
   if (col0 == 0 && B == 1 && c->sym && c->symv) return launch_symv(c, u, accumulate, st);
   if (col0 == 0 && B <= c->gemv_max_b) return launch_gemv(c, B, u, accumulate, st);
   if (col0 == 0 && (c->prec == PIDE_FP64 || c->prec == PIDE_FP32))
     return launch_gemm_simt(c, B, u, accumulate, st);
   return launch_gemm_tc(c, B, u + (size_t)col0 * c->n, accumulate, st, col0);
+}
+
+pide_status launch_apply(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
+                         int col0) {
+  if (B == 0) return PIDE_OK;
+  c->tail.pending = false;
+  const pide_status s = apply_dispatch(c, B, u, accumulate, st, col0);
+  if (s != PIDE_OK) {
+    c->tail.pending = false;
+    return s;
+  }
+  return launch_tail_reduce(c, st);   // after the apply's own profile scope
 }
 
 // Refinement with the FP64 residual of one column group hidden under the
@@ -549,7 +568,8 @@ extern "C" void pide_destroy(pide_handle h) {
   cudaDeviceSynchronize();
   void* ptrs[] = {h->sym, h->sym_lo, h->sym_scale, h->dfl, h->ysum, h->Rf, h->eps, h->cf, h->d, h->dinv, h->w, h->wsp, h->inv, h->inv_lo, h->row_scale, h->R, h->col_scale,
                   h->corr, h->corr_scale, h->Rc, h->col_scale_c,
-                  h->lift, h->colmax, h->flags, h->hist, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out};
+                  h->lift, h->colmax, h->flags, h->hist, h->hbuf_b, h->hbuf_u, h->sbuf_in, h->sbuf_out,
+                  h->tail_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : h->prof_events) {

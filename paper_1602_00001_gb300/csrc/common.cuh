@@ -110,6 +110,16 @@ struct pide_ctx {
   int gemm_a_hint = 2;              // L2 policy of the inverse's TMA loads (policy_for_a)
   int gemm_u_hint = 1;              // epilogue's u loads/stores: 0 plain, 1 L2 evict-first
   int max_pairs = 0;                // SM pairs resident at once for that kernel (queried once)
+  // K-split last round of the SM-pair GEMM: FP32 partial tiles (one 256 x 256
+  // slot per pair, allocated with the workspace) and the reduction that the
+  // GEMM's caller launches after the GEMM's own profile scope
+  float* tail_ws = nullptr;
+  int tail_slots = 0;
+  struct TailReduce {
+    bool pending = false;
+    double* u = nullptr;            // the GEMM's u (already offset to its first column)
+    int B = 0, n_tiles = 0, first_tile = 0, tiles = 0, P = 0, accumulate = 0;
+  } tail;
   int overlap = 0;                  // residual of one column group under the GEMM of the other
   int resid_ctas_per_sm = 2;        // residual grid under a concurrent GEMM (CTAs of 256 per SM)
   cudaStream_t aux = nullptr;       // low-priority stream for the overlapped residuals
@@ -241,6 +251,9 @@ pide_status launch_gemm_tc(pide_ctx* c, int B, double* u, bool accumulate, cudaS
 // the same on pairs of SMs (tcgen05 cta_group::2, 256 x 256 tiles), for B > 128
 pide_status launch_gemm_tc2(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
                             int col0 = 0, bool corr = false);
+// Adds the FP32 partial tiles of a K-split last round (left by the SM-pair GEMM
+// in c->tail) to u, in profile class 4; nothing when none is pending.
+pide_status launch_tail_reduce(pide_ctx* c, cudaStream_t st);
 pide_status launch_gemv(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st);
 pide_status build_sym_store(pide_ctx* c, const double* G, cudaStream_t st);   // G = L^-1 (FP64)
 pide_status launch_symv(pide_ctx* c, double* u, bool accumulate, cudaStream_t st);

@@ -162,8 +162,17 @@ pide_status launch_corr_rhs(pide_ctx* c, int B, cudaStream_t st) {
 
 pide_status launch_apply_corr(pide_ctx* c, int B, double* u, cudaStream_t st) {
   if (B == 0) return PIDE_OK;
-  ProfScope ps(c, st, 3);   // its own class: the FP8 GEMM, timed apart from the BF16 applies
-  return launch_gemm_tc(c, B, u, true, st, 0, true);
+  c->tail.pending = false;
+  pide_status s;
+  {
+    ProfScope ps(c, st, 3);   // its own class: the FP8 GEMM, timed apart from the BF16 applies
+    s = launch_gemm_tc(c, B, u, true, st, 0, true);
+  }
+  if (s != PIDE_OK) {
+    c->tail.pending = false;
+    return s;
+  }
+  return launch_tail_reduce(c, st);
 }
 
 }  // namespace pide

@@ -21,8 +21,14 @@
 // records an error word and leaves through the same teardown (a cluster
 // barrier, then the pair's collective TMEM release).
 //
-// Schedule: the data-parallel waves plus the slab-grouped stream-K tail of the
-// single-SM kernel, in units of clusters and 256 x 256 tiles.
+// Schedule: persistent clusters take whole tiles cid, cid + G, ... (G clusters).
+// When the last round would leave most pairs idle (its r tiles at most G / 2),
+// the whole rounds come first and each of the r tiles is then cut into
+// P = G / r ranges of k-blocks, one per cluster; a piece writes its scaled FP32
+// partial tile to a slot of a workspace and a separate reduction kernel adds
+// the P partials of each tile to u in FP64.  At 198^2 unknowns and B = 1024
+// (616 tiles on 76 pairs: 8 rounds and 8 tiles) the ninth round of whole tiles
+// cost as much as a full one.
 #include "common.cuh"
 
 namespace pide {
@@ -125,41 +131,32 @@ __device__ __forceinline__ void mma_commit_pair_local(uint64_t* bar) {
       : "memory");
 }
 
-// The (tile, k-range) segments of one cluster: as in the single-SM kernel with
-// clusters in place of CTAs.
+// The (tile, k-range) segments of one cluster: whole tiles below dp_tiles,
+// then at most one K-piece of the last round -- clusters cid < pieces = r P take
+// piece q = cid mod P of tile dp_tiles + cid / P, whose partial goes to slot cid.
 struct SegIter2 {
-  int G, T, dp_tiles, num_kb, t_dp, j, base_m;
-  long long u, u1;
-  __device__ SegIter2(int dp, int nkb, int n_tiles, int m_tiles, int sk)
-      : G((int)gridDim.x / 2), T(n_tiles), dp_tiles(dp), num_kb(nkb), t_dp((int)blockIdx.x / 2) {
-    const int cid = (int)blockIdx.x / 2;
-    const int NG = G / T;
-    const int g = cid / T;
-    j = cid - g * T;
-    base_m = dp_tiles / T;
-    const long long U = sk ? (long long)(m_tiles - base_m) * nkb : 0;
-    if (NG > 0 && g < NG) {
-      u = U * g / NG;
-      u1 = U * (g + 1) / NG;
-    } else {
-      u = u1 = 0;
-    }
-  }
-  __device__ bool next(int& tile, int& kb0, int& kb1) {
+  int G, t_dp, dp_tiles, num_kb, P, pieces;
+  bool tail_left;
+  __device__ SegIter2(int dp, int nkb, int P_, int pieces_)
+      : G((int)gridDim.x / 2), t_dp((int)blockIdx.x / 2), dp_tiles(dp), num_kb(nkb), P(P_),
+        pieces(pieces_), tail_left(true) {}
+  __device__ bool next(int& tile, int& kb0, int& kb1, int& slot) {
     if (t_dp < dp_tiles) {
       tile = t_dp;
       kb0 = 0;
       kb1 = num_kb;
+      slot = -1;
       t_dp += G;
       return true;
     }
-    if (u < u1) {
-      const int m = base_m + (int)(u / num_kb);
-      tile = m * T + j;
-      kb0 = (int)(u % num_kb);
-      const long long left = u1 - u;
-      kb1 = (kb0 + left < num_kb) ? kb0 + (int)left : num_kb;
-      u += kb1 - kb0;
+    const int cid = (int)blockIdx.x / 2;
+    if (tail_left && cid < pieces) {
+      tail_left = false;
+      const int t = cid / P, q = cid - t * P;
+      tile = dp_tiles + t;
+      kb0 = (int)((long long)num_kb * q / P);
+      kb1 = (int)((long long)num_kb * (q + 1) / P);
+      slot = cid;
       return true;
     }
     return false;
@@ -172,9 +169,9 @@ template <int STAGES, int MODE, int NACC>   // MODE 0: BF16, 1: FP8 (hi only), 2
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
                 const __grid_constant__ CUtensorMap tmR, int n, int B, int rrow0, int num_kb,
-                int dp_tiles, int sk, double* __restrict__ u, int accumulate,
+                int dp_tiles, int P, int pieces, double* __restrict__ u, int accumulate,
                 const float* __restrict__ row_scale, const float* __restrict__ col_scale,
-                uint32_t* __restrict__ flags, int a_hint, int u_hint) {
+                float* __restrict__ ws, uint32_t* __restrict__ flags, int a_hint, int u_hint) {
   constexpr bool FP8 = MODE == 1 || MODE == 2;   // kind::f8f6f4 (else kind::f16)
   constexpr bool SCALED = MODE != 0;              // epilogue applies row and column scales
   constexpr bool LO = MODE == 2;
@@ -241,9 +238,9 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int s = 0;
     uint32_t ph = 0;
     bool ok = true;
-    SegIter2 it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
-    int tile, kb0, kb1;
-    while (ok && it.next(tile, kb0, kb1)) {
+    SegIter2 it(dp_tiles, num_kb, P, pieces);
+    int tile, kb0, kb1, slot;
+    while (ok && it.next(tile, kb0, kb1, slot)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
       const int arow = mt * BM2 + (int)rank * HALF;
       const int rrow = rrow0 + nt * BN2 + (int)rank * HALF;
@@ -280,9 +277,9 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int acc = 0;
     uint32_t acc_ph = 0;
     bool ok = true;
-    SegIter2 it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
-    int tile, kb0, kb1;
-    while (ok && it.next(tile, kb0, kb1)) {
+    SegIter2 it(dp_tiles, num_kb, P, pieces);
+    int tile, kb0, kb1, slot;
+    while (ok && it.next(tile, kb0, kb1, slot)) {
       if (!mbar_wait_bounded(&tempty[acc], acc_ph ^ 1, abort_s)) {
         ok = false;
         break;
@@ -336,11 +333,10 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const int row_in_tile = quarter * 32 + lane;
     int acc = 0;
     uint32_t acc_ph = 0;
-    SegIter2 it(dp_tiles, num_kb, n_tiles, m_tiles, sk);
-    int tile, kb0, kb1;
-    while (it.next(tile, kb0, kb1)) {
+    SegIter2 it(dp_tiles, num_kb, P, pieces);
+    int tile, kb0, kb1, slot;
+    while (it.next(tile, kb0, kb1, slot)) {
       const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
-      const bool whole = (kb0 == 0 && kb1 == num_kb);
       bool ok = mbar_wait_bounded(&tfull[acc], acc_ph, abort_s);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
@@ -361,11 +357,27 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         tmem_ld_32x32b_x32(tbase + ch * 32, v);
         tmem_ld_wait();
         const int colbase = nt * BN2 + ch * 32;
-        if (prow) {
+        if (slot >= 0) {
+          // a K-piece: the scaled partial to its slot, [column][row] within the
+          // tile (a warp stores 32 consecutive rows of one column); zero outside
+          // the rows and columns of u
+          float* wcol = ws + (size_t)slot * (BM2 * BN2) + (size_t)(ch * 32) * BM2 +
+                        (int)rank * HALF + row_in_tile;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = colbase + j;
+            float a = 0.0f;
+            if (prow && col < B) {
+              a = __uint_as_float(v[j]);
+              if (SCALED) a = a * rs * col_scale[col];
+            }
+            wcol[(size_t)j * BM2] = a;
+          }
+        } else if (prow) {
           // the 32 old values first: loads issued together instead of one
           // load-add-store round trip per column
           double old[32];
-          if (accumulate && whole) {
+          if (accumulate) {
             if (u_hint) {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
@@ -384,8 +396,7 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               if (SCALED) a = a * rs * col_scale[col];
               const double val = f32_to_f64(a);
               double* dst = u + (size_t)col * n + p;
-              if (!whole) atomicAdd(dst, val);
-              else if (u_hint) st_f64_hint(dst, accumulate ? old[j] + val : val, upol);
+              if (u_hint) st_f64_hint(dst, accumulate ? old[j] + val : val, upol);
               else *dst = accumulate ? old[j] + val : val;
             }
           }
@@ -410,11 +421,40 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   if (warp == 1) tmem_dealloc_pair(tmem_base, TMEM_COLS);
 }
 
+// u (=|+=) the sum of the P partial tiles of each tile of the K-split last
+// round, in FP64 and in piece order.  Block (x, t): 256 consecutive rows of one
+// column of tail tile t, so partial loads and u accesses are coalesced.
+__global__ void __launch_bounds__(256)
+tail_reduce_kernel(double* __restrict__ u, const float* __restrict__ ws, int n, int B,
+                   int n_tiles, int first_tile, int P, int accumulate,
+                   const uint32_t* __restrict__ flags) {
+  if (flags[FLAG_DONE]) return;
+  const int t = (int)blockIdx.y;
+  const int tile = first_tile + t;
+  const int mt = tile / n_tiles, nt = tile - mt * n_tiles;
+  const int e = (int)blockIdx.x * 256 + (int)threadIdx.x;   // column-in-tile * 256 + row
+  const int p = mt * BM2 + (e & (BM2 - 1));
+  const int col = nt * BN2 + (e >> 8);
+  if (p >= n || col >= B) return;
+  const float* src = ws + (size_t)t * P * (BM2 * BN2) + e;
+  double sum = 0.0;
+  for (int q = 0; q < P; ++q) sum += f32_to_f64(src[(size_t)q * (BM2 * BN2)]);
+  double* dst = u + (size_t)col * n + p;
+  *dst = accumulate ? *dst + sum : sum;
+}
+
 }  // namespace
 
-// Zeroing of the stream-K tiles is shared with the single-SM kernel.
-pide_status launch_zero_tiles(pide_ctx* c, double* u, int B, int bm, int bn, int n_tiles,
-                              int first_tile, int count, cudaStream_t st);
+pide_status launch_tail_reduce(pide_ctx* c, cudaStream_t st) {
+  if (!c->tail.pending) return PIDE_OK;
+  const pide_ctx::TailReduce t = c->tail;
+  c->tail.pending = false;
+  ProfScope ps(c, st, 4);
+  tail_reduce_kernel<<<dim3(BM2 * BN2 / 256, t.tiles), 256, 0, st>>>(
+      t.u, c->tail_ws, c->n, t.B, t.n_tiles, t.first_tile, t.P, t.accumulate, c->flags);
+  PIDE_CUDA_TRY(cudaGetLastError());
+  return PIDE_OK;
+}
 
 template <int STAGES, int MODE, int NACC>
 static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cudaStream_t st,
@@ -440,32 +480,39 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const int tiles = m_tiles * n_tiles;
   constexpr int KE = (MODE == 1 || MODE == 2) ? 128 : 64;   // K elements per stage
   const int num_kb = (c->n + KE - 1) / KE;
-  // The stream-K tail pays only when the data-parallel waves are few: at 198^2,
-  // B = 1024 (8.1 waves) it measured the same time as whole tiles but 1.3-1.5 GB
-  // more DRAM reads per launch; at B = 256 (2.0 waves) whole tiles would idle
-  // half the pairs for a third of the launch.
-  const bool few_waves = tiles < 4 * G;
-  int clusters, dp_tiles;
-  if (!c->gemm_streamk || !few_waves || tiles % G == 0 || n_tiles > G) {
-    clusters = tiles < G ? tiles : G;
-    dp_tiles = tiles;
-  } else {
-    clusters = G;
-    dp_tiles = tiles < G ? 0 : ((tiles / G - 1) * G / n_tiles) * n_tiles;
+  // Whole rounds of tiles, then the last round's r tiles cut along K when
+  // they would leave at least half of the pairs idle: P = G / r pieces of at
+  // least 8 k-blocks per tile.
+  const int full = tiles / G, rest = tiles - full * G;
+  int P = 0;
+  if (c->gemm_streamk && rest > 0) {
+    P = G / rest;
+    if (P > num_kb / 8) P = num_kb / 8;
+    if (P < 2 || rest * P > c->tail_slots || !c->tail_ws) P = 0;
   }
-  const int sk = dp_tiles < tiles ? 1 : 0;
-  if (sk && !accumulate)
-    PIDE_TRY(launch_zero_tiles(c, u, B, BM2, BN2, n_tiles, dp_tiles, tiles - dp_tiles, st));
+  const int clusters = P ? G : (tiles < G ? tiles : G);
+  const int dp_tiles = P ? full * G : tiles;
+  const int pieces = P ? rest * P : 0;
   // the correction term: e4m3 C against Rc, scales s_p (rows) and t_j (columns)
   const CUtensorMap& A = corr ? c->tmA_corr : c->tmA;
   const CUtensorMap& Alo = corr ? c->tmA_corr : c->tmA_lo;
   const CUtensorMap& R = corr ? c->tmRc : c->tmR;
   const float* rs = corr ? c->corr_scale : c->row_scale;
   const float* cs = corr ? c->col_scale_c + col0 : (MODE != 0 ? c->col_scale + col0 : nullptr);
-  kern<<<2 * clusters, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, sk, u,
-                                        accumulate ? 1 : 0, rs, cs, c->flags, c->gemm_a_hint,
-                                c->gemm_u_hint);
+  kern<<<2 * clusters, 192, smem, st>>>(A, Alo, R, c->n, B, col0, num_kb, dp_tiles, P, pieces,
+                                        u, accumulate ? 1 : 0, rs, cs, c->tail_ws, c->flags,
+                                        c->gemm_a_hint, c->gemm_u_hint);
   PIDE_CUDA_TRY(cudaGetLastError());
+  if (P) {
+    c->tail.pending = true;
+    c->tail.u = u;
+    c->tail.B = B;
+    c->tail.n_tiles = n_tiles;
+    c->tail.first_tile = dp_tiles;
+    c->tail.tiles = rest;
+    c->tail.P = P;
+    c->tail.accumulate = accumulate ? 1 : 0;
+  }
   return PIDE_OK;
 }
 
