@@ -210,12 +210,15 @@ def test_3d_refined():
 
 
 @pytest.mark.parametrize("prec,nx,ny,B", [("fp16_fp8", 40, 33, 300), ("fp16", 23, 61, 5),
+                                          ("fp16_fp8", 23, 61, 333), ("fp16", 5, 6, 7),
                                           ("fp16_fp8", 200, 200, 64)])
 def test_cluster_prep_equals_one_cta_prep(prec, nx, ny, B):
     """The FP16 prep with a CTA cluster per column (one HBM pass, the e4m3 copy
     of R for the correction term written in the same pass) gives bit for bit
     the solution of the one-CTA prep followed by the separate e4m3 copy: with
-    boundary values, with a column of zeros, and for the adjoint's f = b / d."""
+    boundary values, with a column of zeros, for the adjoint's f = b / d, for
+    an odd number of unknowns (n = 1239 at 23 x 61) and for quarters of 8, 4,
+    0 and 0 unknowns (n = 12 at 5 x 6)."""
     h = 1.0 / (max(nx, ny) - 1)
     eps = W.eps_lognormal(nx, ny, seed=nx * ny)
     b = _b(nx, ny, h, eps, B, seed=31)
@@ -232,3 +235,27 @@ def test_cluster_prep_equals_one_cta_prep(prec, nx, ny, B):
     assert torch.equal(outs[1][0], outs[0][0]) and torch.equal(outs[1][1], outs[0][1])
     s.close()
 
+
+
+def test_cluster_prep_on_a_view_8_bytes_off_16():
+    """Right-hand sides that start 8 bytes past a 16-byte boundary (a view one
+    element into a larger tensor): the cluster prep's solution equals the
+    one-CTA prep's bit for bit."""
+    nx, ny = 23, 61
+    h = 1.0 / 60
+    eps = W.eps_lognormal(nx, ny, seed=77)
+    B = 97
+    b = _b(nx, ny, h, eps, B, seed=78)
+    n = b.shape[1]
+    big = torch.zeros(B * n + 1, dtype=torch.float64, device="cuda")
+    big[1:] = torch.from_numpy(b).cuda().reshape(-1)
+    bv = big[1:].view(B, n)
+    assert bv.data_ptr() % 16 == 8
+    s = _solver(nx, ny, h, eps, "fp16_fp8")
+    s.set_tuning(gemm_streamk=0)          # whole tiles: no atomic partial sums
+    outs = {}
+    for pc in (1, 0):
+        s.set_tuning(prep_cluster=pc)
+        outs[pc] = s.apply(bv, sweeps=1)
+    assert torch.equal(outs[1], outs[0])
+    s.close()
