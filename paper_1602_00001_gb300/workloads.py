@@ -1,7 +1,9 @@
 """Seeded synthetic inputs shared by the CUDA path, its tests and the oracle.
 
 This module holds no arithmetic of the method itself: it only draws node
-permittivity fields and charge densities with numpy's seeded generator.  The
+permittivity fields and charge densities with numpy's seeded generator, and
+evaluates the closed-form source and solution of the paper's worked example
+(Eqs. 4-5) as inputs.  The
 node grid follows Eq. (2): ``nx`` nodes along x (index j, fastest), ``ny``
 along y (index i), spacing ``h`` in both directions, boundary nodes included.
 Interior arrays are returned in the order of Fig. 3 restricted to the
@@ -22,6 +24,18 @@ def node_coords(nx: int, ny: int, h: float):
     x = h * np.arange(nx, dtype=np.float64)
     y = h * np.arange(ny, dtype=np.float64)
     return np.meshgrid(x, y)  # each [ny][nx]
+
+
+def example_source(x, y):
+    """The worked example's right side (Eq. 4) at node coordinates x, y: an
+    input, like the seeded fields below."""
+    return (12 * x ** 2 - 6 * x) * (y ** 3 - y ** 2) + (x ** 4 - x ** 3) * (6 * y - 2)
+
+
+def example_exact(x, y):
+    """The worked example's exact solution (Eq. 5) at node coordinates x, y:
+    the reference its discrete solutions are measured against."""
+    return (x ** 4 - x ** 3) * (y ** 3 - y ** 2)
 
 
 def eps_uniform(nx: int, ny: int) -> np.ndarray:
