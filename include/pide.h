@@ -500,10 +500,10 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *                           tile); each width present in a plan is one launch per phase
  *   PIDE_TUNE_BATCH_TN        SIMT tiles: width 16, 32 or 64 columns (0 = default: the narrowest
  *                           covering the problem's B)
- *   PIDE_TUNE_PREP_CLUSTER    FP16 right-hand-side prep: 1 (default) = a cluster of 4 CTAs per
+ *   PIDE_TUNE_PREP_CLUSTER    FP16 right-hand-side prep: 1 (default) = a cluster of 8 CTAs per
  *                           column holds the column in shared memory (one HBM pass; with the
  *                           correction term in the first apply it also writes the e4m3 copy of R),
- *                           up to ~56K unknowns; 0 = one CTA per column reading it twice */
+ *                           up to ~112K unknowns; 0 = one CTA per column reading it twice */
 typedef enum {
   PIDE_TUNE_GEMV_THREADS = 0,
   PIDE_TUNE_GEMV_UNROLL = 1,

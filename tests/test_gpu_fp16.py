@@ -217,8 +217,8 @@ def test_cluster_prep_equals_one_cta_prep(prec, nx, ny, B):
     of R for the correction term written in the same pass) gives bit for bit
     the solution of the one-CTA prep followed by the separate e4m3 copy: with
     boundary values, with a column of zeros, for the adjoint's f = b / d, for
-    an odd number of unknowns (n = 1239 at 23 x 61) and for quarters of 8, 4,
-    0 and 0 unknowns (n = 12 at 5 x 6)."""
+    an odd number of unknowns (n = 1239 at 23 x 61) and for CTA slices of 8,
+    4 and 0 unknowns (n = 12 at 5 x 6)."""
     h = 1.0 / (max(nx, ny) - 1)
     eps = W.eps_lognormal(nx, ny, seed=nx * ny)
     b = _b(nx, ny, h, eps, B, seed=31)
