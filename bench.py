@@ -528,6 +528,9 @@ def threed_workload(args):
     # with the correction term 282k, BF16 215k in two sweeps), so FP16 is the default
     prec = args.precision if args.precision in ("bf16", "bf16_fp8", "fp16", "fp16_fp8") else "fp16"
     s = Solver3D(N, N, N, h, eps, prec)
+    tune = dict(kv.split("=", 1) for kv in args.tune)
+    if tune:
+        s.set_tuning(**{kk: int(v) for kk, v in tune.items()})
     s.reserve(B)
     u = torch.empty_like(b)
     errs = {}

@@ -437,12 +437,16 @@ pide_status pide_round_inverse_decimal(pide_handle h, int32_t digits, void* stre
  *   PIDE_TUNE_GEMM_BN       tensor-core tile width for B > 128: 128 or 256 (default 256)
  *   PIDE_TUNE_GEMM_STREAMK  1 (default): split the last partial wave of tiles over all SMs by
  *                           k-blocks.  Single SMs (B <= 128 or GEMM_BN 128): FP64 atomic
- *                           partial sums.  SM pairs: when the last round holds at most
- *                           half as many tiles as there are pairs, each of its tiles is
- *                           cut into P = pairs / tiles K-ranges (at least 8 k-blocks each),
- *                           the pieces write FP32 partial tiles to a handle-owned buffer
- *                           and a reduction kernel adds them to u in FP64, in piece
- *                           order (deterministic); 0: whole tiles only
+ *                           partial sums.  SM pairs: the r tiles of the last partial
+ *                           round are cut into P K-ranges each (at least 8 k-blocks),
+ *                           dealt round-robin to the pairs, with P chosen to shorten that
+ *                           round plus the reduction the most, and only when that saves
+ *                           5 % of a tile (e.g. r = 8 of 76 pairs at 198^2: P = 8); the
+ *                           pieces write FP32 partial tiles to a handle-owned buffer (80
+ *                           MB at 152 SMs) and a reduction kernel adds them to u, in
+ *                           piece order (deterministic).  2: the same, leaving the
+ *                           reduction's cost out of the choice (r = 56: P = 4, three
+ *                           pieces on most pairs); 0: whole tiles only
  *   PIDE_TUNE_OVERLAP       1: for B >= 512 with tol <= 0, split the columns in
  *                           two groups and run each group's FP64 residual on a
  *                           low-priority internal stream under the other group's

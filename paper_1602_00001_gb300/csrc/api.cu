@@ -132,11 +132,11 @@ pide_status make_tma_rhs_corr(pide_ctx* c, int bn) {
 // ---------------------------------------------------------------- workspace
 
 pide_status ensure_workspace(pide_ctx* c, int B) {
-  // the SM-pair GEMM's partial tiles: one 256 x 256 FP32 slot per pair (20 MB
-  // at 152 SMs), allocated once so that a captured apply allocates nothing
+  // the SM-pair GEMM's partial tiles: four 256 x 256 FP32 slots per pair (80
+  // MB at 152 SMs), allocated once so that a captured apply allocates nothing
   if (!c->tail_ws && (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2 ||
                       c->prec == PIDE_FP16)) {
-    const int slots = c->num_sms / 2 > 0 ? c->num_sms / 2 : 1;
+    const int slots = 4 * (c->num_sms / 2 > 0 ? c->num_sms / 2 : 1);
     PIDE_CUDA_TRY(cudaMalloc((void**)&c->tail_ws, (size_t)slots * 256 * 256 * sizeof(float)));
     c->tail_slots = slots;
   }
@@ -1095,7 +1095,7 @@ extern "C" pide_status pide_set_tuning(pide_handle h, int32_t key, int32_t value
       h->gemm_bn_large = value;
       return PIDE_OK;
     case PIDE_TUNE_GEMM_STREAMK:
-      if (value != 0 && value != 1) break;
+      if (value < 0 || value > 2) break;
       h->gemm_streamk = value;
       return PIDE_OK;
     case PIDE_TUNE_OVERLAP:

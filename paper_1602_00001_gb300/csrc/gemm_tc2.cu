@@ -131,15 +131,17 @@ __device__ __forceinline__ void mma_commit_pair_local(uint64_t* bar) {
       : "memory");
 }
 
-// The (tile, k-range) segments of one cluster: whole tiles below dp_tiles,
-// then at most one K-piece of the last round -- clusters cid < pieces = r P take
-// piece q = cid mod P of tile dp_tiles + cid / P, whose partial goes to slot cid.
+// The (tile, k-range) segments of one cluster: whole tiles cid, cid + G, ...
+// below dp_tiles, then the pieces of the last round: piece g = cid, cid + G,
+// ... below pieces = r P is piece q = g mod P of tile dp_tiles + g / P, and
+// its partial goes to slot g.  Pieces are numbered tile by tile, so the
+// clusters that run at the same time hold the same K-range of neighbouring
+// tiles (the column tiles of one slab share their A rows in L2).
 struct SegIter2 {
-  int G, t_dp, dp_tiles, num_kb, P, pieces;
-  bool tail_left;
+  int G, t_dp, dp_tiles, num_kb, P, pieces, g;
   __device__ SegIter2(int dp, int nkb, int P_, int pieces_)
       : G((int)gridDim.x / 2), t_dp((int)blockIdx.x / 2), dp_tiles(dp), num_kb(nkb), P(P_),
-        pieces(pieces_), tail_left(true) {}
+        pieces(pieces_), g((int)blockIdx.x / 2) {}
   __device__ bool next(int& tile, int& kb0, int& kb1, int& slot) {
     if (t_dp < dp_tiles) {
       tile = t_dp;
@@ -149,14 +151,13 @@ struct SegIter2 {
       t_dp += G;
       return true;
     }
-    const int cid = (int)blockIdx.x / 2;
-    if (tail_left && cid < pieces) {
-      tail_left = false;
-      const int t = cid / P, q = cid - t * P;
+    if (g < pieces) {
+      const int t = g / P, q = g - t * P;
       tile = dp_tiles + t;
       kb0 = (int)((long long)num_kb * q / P);
       kb1 = (int)((long long)num_kb * (q + 1) / P);
-      slot = cid;
+      slot = g;
+      g += G;
       return true;
     }
     return false;
@@ -422,8 +423,13 @@ gemm_tc2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 }
 
 // u (=|+=) the sum of the P partial tiles of each tile of the K-split last
-// round, in FP64 and in piece order.  Block (x, t): 256 consecutive rows of one
-// column of tail tile t, so partial loads and u accesses are coalesced.
+// round, in piece order.  Block (x, t): 256 consecutive rows of one column of
+// tail tile t, so partial loads and u accesses are coalesced.  The partials
+// are summed as a float pair with Knuth's two-sum (each step exact in its high
+// part, ~2^-48 of the sum in all) and widened to FP64 with integer operations:
+// two FP64 additions per element instead of 2P + 1 conversions and additions
+// on GB300's narrow FP64 pipe, which bounded the first version (56 tiles of 4
+// pieces: 68 us, as long as reading the partials alone).
 __global__ void __launch_bounds__(256)
 tail_reduce_kernel(double* __restrict__ u, const float* __restrict__ ws, int n, int B,
                    int n_tiles, int first_tile, int P, int accumulate,
@@ -436,11 +442,21 @@ tail_reduce_kernel(double* __restrict__ u, const float* __restrict__ ws, int n, 
   const int p = mt * BM2 + (e & (BM2 - 1));
   const int col = nt * BN2 + (e >> 8);
   if (p >= n || col >= B) return;
-  const float* src = ws + (size_t)t * P * (BM2 * BN2) + e;
-  double sum = 0.0;
-  for (int q = 0; q < P; ++q) sum += f32_to_f64(src[(size_t)q * (BM2 * BN2)]);
   double* dst = u + (size_t)col * n + p;
-  *dst = accumulate ? *dst + sum : sum;
+  const double old = accumulate ? *dst : 0.0;
+  const float* src = ws + (size_t)t * P * (BM2 * BN2) + e;
+  float sh = 0.0f, sl = 0.0f;
+#pragma unroll 4
+  for (int q = 0; q < P; ++q) {
+    const float x = src[(size_t)q * (BM2 * BN2)];
+    const float s = __fadd_rn(sh, x);
+    const float v = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(x, v));
+    sh = s;
+    sl = __fadd_rn(sl, err);
+  }
+  const double sum = f32_to_f64(sh) + f32_to_f64(sl);
+  *dst = accumulate ? old + sum : sum;
 }
 
 }  // namespace
@@ -480,15 +496,32 @@ static pide_status launch_tc2(pide_ctx* c, int B, double* u, bool accumulate, cu
   const int tiles = m_tiles * n_tiles;
   constexpr int KE = (MODE == 1 || MODE == 2) ? 128 : 64;   // K elements per stage
   const int num_kb = (c->n + KE - 1) / KE;
-  // Whole rounds of tiles, then the last round's r tiles cut along K when
-  // they would leave at least half of the pairs idle: P = G / r pieces of at
-  // least 8 k-blocks per tile.
+  // Whole rounds of tiles, then the last round's r tiles cut along K into P
+  // pieces each (at least 8 k-blocks), dealt round-robin to the G pairs: the
+  // round then takes ceil(r P / G) / P of a tile's time instead of one, and the
+  // reduction of the r P partial tiles about as long as half a k-block each
+  // (measured: 8 x 9 partials in 11 us, 56 x 4 in 37 us, against 0.34 us per
+  // k-block of 64).  P minimises the sum (the smallest P within 1 % of a tile
+  // of the best); no split unless it saves 5 % of a tile.  At 198^2, B = 1024:
+  // r = 8 of G = 76, P = 8.  With gemm_streamk = 2 the reduction's cost is left
+  // out (any split that shortens the round by 1 % is taken).
   const int full = tiles / G, rest = tiles - full * G;
   int P = 0;
-  if (c->gemm_streamk && rest > 0) {
-    P = G / rest;
-    if (P > num_kb / 8) P = num_kb / 8;
-    if (P < 2 || rest * P > c->tail_slots || !c->tail_ws) P = 0;
+  if (c->gemm_streamk && rest > 0 && c->tail_ws) {
+    int pmax = num_kb / 8;
+    if (pmax > c->tail_slots / rest) pmax = c->tail_slots / rest;
+    const double per_partial = c->gemm_streamk == 2 ? 0.0 : 0.5;
+    auto cost = [&](int p) {
+      return (double)((rest * p + G - 1) / G) / p + per_partial * rest * p / num_kb;
+    };
+    double best = 1.0;
+    for (int p = 2; p <= pmax; ++p) best = cost(p) < best ? cost(p) : best;
+    if (best < (c->gemm_streamk == 2 ? 0.99 : 0.95))
+      for (int p = 2; p <= pmax; ++p)
+        if (cost(p) <= best + 0.01) {
+          P = p;
+          break;
+        }
   }
   const int clusters = P ? G : (tiles < G ? tiles : G);
   const int dp_tiles = P ? full * G : tiles;

@@ -1,10 +1,14 @@
 """The SM-pair tensor-core apply with its last round of tiles cut along K.
 
-When the last round of 256 x 256 tiles would leave at least half of the SM
-pairs idle, each of its tiles is split into K-ranges whose FP32 partial tiles a
-reduction kernel adds to u in FP64.  On a 60 x 60 node grid (n = 3364, 14 row
-slabs of 256) with ~76 pairs: B = 300 gives 28 tiles (no whole round, every
-tile split), B = 1600 gives 98 tiles (one whole round, then 22 split tiles),
+The tiles of the last partial round of 256 x 256 tiles are split into
+K-ranges whose FP32 partial tiles a reduction kernel adds to u in FP64.  The
+default weighs the reduction's cost and does not split at these small sizes;
+the tests take gemm_streamk = 2, which leaves that cost out.  On a 60 x 60 node
+grid (n = 3364, 14 row slabs of 256; 53 k-blocks of 64, 27 of
+128 for the e4m3 correction) with 76 pairs: B = 300 gives 28 tiles (no whole
+round, every tile in 5 pieces), B = 1600 gives 98 tiles (one whole round, then
+22 tiles in 3 pieces), B = 1024 gives 56 tiles in 4 pieces (three pieces on
+most pairs; the correction GEMM's 27 k-blocks allow no gain: whole tiles),
 B = 1200 gives 70 tiles (no split: the last round is nearly full).  Each
 result is checked against the oracle's exact contraction of the same rounded
 operands (the bound of the FP32 accumulation), against the whole-tile schedule,
@@ -47,9 +51,11 @@ def _b(eps, B, seed):
     return O.rhs_from_charge(NX, NY, H, eps, rho)
 
 
-def _solver(eps, prec):
+def _solver(eps, prec, streamk=2):
     from paper_1602_00001_gb300.binding import Solver
-    return Solver(NX, NY, H, eps, prec)
+    s = Solver(NX, NY, H, eps, prec)
+    s.set_tuning(gemm_streamk=streamk)
+    return s
 
 
 def _expected(linv, b, prec):
@@ -82,7 +88,11 @@ def _accumulation_bound(n):
     return 2.0 * steps * 2.0 ** -23
 
 
-@pytest.mark.parametrize("B", [300, 1600, 1200])
+# reduction launches of one unrefined apply: (FP16 / BF16 GEMM, e4m3 correction GEMM)
+REDUCES = {300: (1, 1), 1600: (1, 1), 1024: (1, 0), 1200: (0, 0)}
+
+
+@pytest.mark.parametrize("B", [300, 1600, 1024, 1200])
 @pytest.mark.parametrize("prec", ["fp16", "fp16_fp8", "bf16"])
 def test_first_apply_is_exact_contraction(eps, linv, prec, B):
     b = _b(eps, B, seed=B + 7)
@@ -95,19 +105,16 @@ def test_first_apply_is_exact_contraction(eps, linv, prec, B):
     j, p = np.unravel_index(np.argmax(ratio), ratio.shape)
     tile = (p // 256) * ((B + 255) // 256) + j // 256
     assert ratio.max() <= _accumulation_bound(s.n), (float(ratio.max()), int(p), int(j), int(tile))
-    gemms = 2 if prec == "fp16_fp8" else 1
-    if B in (300, 1600):
-        assert prof["reduce"][0] == gemms, prof
-    else:
-        assert prof["reduce"][0] == 0, prof
+    main, corr = REDUCES[B]
+    assert prof["reduce"][0] == main + (corr if prec == "fp16_fp8" else 0), prof
     s.close()
 
 
+@pytest.mark.parametrize("B", [1600, 1024])
 @pytest.mark.parametrize("prec", ["fp16_fp8", "bf16"])
-def test_split_matches_whole_tiles_and_repeats(eps, prec):
+def test_split_matches_whole_tiles_and_repeats(eps, prec, B):
     """Same contraction as whole tiles up to FP32 partial-sum rounding (bounded by
     the magnitudes, L^-1 >= 0); two runs of the split schedule are identical."""
-    B = 1600
     b = _b(eps, B, seed=5)
     s = _solver(eps, prec)
     bd = torch.from_numpy(b).cuda()
@@ -160,9 +167,29 @@ def test_tiny_grid_keeps_whole_tiles():
     b = O.rhs_from_charge(nx, ny, h, e, rho)
     from paper_1602_00001_gb300.binding import Solver
     s = Solver(nx, ny, h, e, "bf16")
+    s.set_tuning(gemm_streamk=2)
     with s.profile() as prof:
         u = s.apply(b, sweeps=4).cpu().numpy()
     assert prof["reduce"][0] == 0
     ref = (O.interior_inverse(nx, ny, e) @ b.T).T
     assert O.rel_error_eq6(u, ref) < 1e-6
     s.close()
+
+
+def test_default_weighs_the_reduction(eps):
+    """The default (gemm_streamk = 1) counts each partial tile's reduction as
+    half a k-block: at 53 k-blocks per tile the 28 tiles of B = 300 stay whole
+    (140 partial tiles would cost more than the 0.6 of a tile they save), while
+    gemm_streamk = 2 splits them; both equal the oracle's contraction."""
+    B = 300
+    b = _b(eps, B, seed=13)
+    res = {}
+    for sk in (1, 2):
+        s = _solver(eps, "fp16", streamk=sk)
+        with s.profile() as prof:
+            res[sk] = s.apply(b, sweeps=0)
+        assert prof["reduce"][0] == (0 if sk == 1 else 1), (sk, prof)
+        if sk == 2:
+            mag = s.apply(np.abs(b), sweeps=0)     # L^-1 >= 0: the contraction of |b|
+        s.close()
+    assert bool(((res[1] - res[2]).abs() <= 1e-4 * mag + 1e-300).all())
