@@ -327,71 +327,86 @@ __global__ void colmax_b_kernel(const double* __restrict__ b, int n, int mode,
 // Adjoint, per node a of the grid: dLoss/deps_a = sum over the node's faces f
 // (to node b) of T_f * 2 eps_b^2 / (eps_a + eps_b)^2, where
 //   T_f = sum_cols mu_p b_p + mu_q b_q - (mu_p - mu_q)(u_p - u_q)
-// and a boundary endpoint contributes mu = 0, no b term and u = 0.  Each node
-// gathers its own faces (no atomics; each face total is formed twice).
-__global__ void face_grad_kernel(const double* __restrict__ mu, const double* __restrict__ u,
-                                 const double* __restrict__ b, const double* __restrict__ eps,
-                                 int nx, int ny, int B, double* __restrict__ deps) {
-  const int mx = nx - 2, n = mx * (ny - 2);
-  const int N = nx * ny;
-  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N;
-       node += gridDim.x * blockDim.x) {
-    const int i = node / nx, j = node - i * nx;
-    const bool in_a = (i > 0 && i < ny - 1 && j > 0 && j < nx - 1);
-    const int pa = in_a ? (i - 1) * mx + (j - 1) : -1;
-    const double ea = eps[node];
-    double acc = 0.0;
-    const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
-    for (int k = 0; k < 4; ++k) {
-      const int i2 = i + di[k], j2 = j + dj[k];
-      if (i2 < 0 || i2 >= ny || j2 < 0 || j2 >= nx) continue;
-      const bool in_b = (i2 > 0 && i2 < ny - 1 && j2 > 0 && j2 < nx - 1);
-      if (!in_a && !in_b) continue;
-      const int pb = in_b ? (i2 - 1) * mx + (j2 - 1) : -1;
-      double T = 0.0;
-      for (int c = 0; c < B; ++c) {
+// and a boundary endpoint contributes mu = 0, no b term and u = 0.
+//
+// Two passes.  face_t_kernel forms T_f once per face -- the faces toward the
+// +x, +y (and +z) neighbour of every node -- in a block of 32 consecutive
+// nodes (coalesced loads of mu, u and b) by FG_GROUPS column groups whose
+// partial sums are added in group order through shared memory.
+// face_combine_kernel then gives each node the sum over its faces in the
+// order -x, +x, -y, +y (-z, +z).  Both are deterministic.  The first version
+// (one thread per node looping over all B columns of its faces, every face
+// formed twice) took 88 us for a 128^2 grid at B = 32 on GB300's FP64 pipe.
+constexpr int FG_GROUPS = 8;
+
+template <int DIMS>
+__global__ void __launch_bounds__(32 * FG_GROUPS)
+face_t_kernel(const double* __restrict__ mu, const double* __restrict__ u,
+              const double* __restrict__ b, int nx, int ny, int nz, int B,
+              double* __restrict__ Tf) {
+  __shared__ double part[FG_GROUPS][32];
+  const int mx = nx - 2, my = ny - 2, mz = DIMS == 3 ? nz - 2 : 1;
+  const int n = mx * my * mz;
+  const int nzz = DIMS == 3 ? nz : 1;
+  const int N = nx * ny * nzz;
+  const int node = (int)blockIdx.x * 32 + (int)threadIdx.x;
+  const int g = (int)threadIdx.y;
+  const int j = node % nx, i = (node / nx) % ny, l = DIMS == 3 ? node / (nx * ny) : 0;
+  const bool valid = node < N;
+  const bool in_a = valid && (DIMS != 3 || (l > 0 && l < nz - 1)) && i > 0 && i < ny - 1 &&
+                    j > 0 && j < nx - 1;
+  const int pa = in_a ? ((DIMS == 3 ? (l - 1) * my : 0) + (i - 1)) * mx + (j - 1) : -1;
+#pragma unroll
+  for (int d = 0; d < DIMS; ++d) {
+    const int j2 = j + (d == 0), i2 = i + (d == 1), l2 = l + (d == 2);
+    const bool exists = valid && j2 < nx && i2 < ny && l2 < nzz;
+    const bool in_b = exists && (DIMS != 3 || (l2 > 0 && l2 < nz - 1)) && i2 > 0 &&
+                      i2 < ny - 1 && j2 > 0 && j2 < nx - 1;
+    double T = 0.0;
+    if (in_a || in_b) {
+      const int pb = in_b ? ((DIMS == 3 ? (l2 - 1) * my : 0) + (i2 - 1)) * mx + (j2 - 1) : -1;
+      for (int c = g; c < B; c += FG_GROUPS) {
         const size_t o = (size_t)c * n;
         const double mua = in_a ? mu[o + pa] : 0.0, mub = in_b ? mu[o + pb] : 0.0;
         const double ua = in_a ? u[o + pa] : 0.0, ub = in_b ? u[o + pb] : 0.0;
         const double ba = in_a ? b[o + pa] : 0.0, bb = in_b ? b[o + pb] : 0.0;
         T += mua * ba + mub * bb - (mua - mub) * (ua - ub);
       }
-      const double eb = eps[i2 * nx + j2];
-      acc += T * 2.0 * eb * eb / ((ea + eb) * (ea + eb));
     }
-    deps[node] += acc;
+    part[g][threadIdx.x] = T;
+    __syncthreads();
+    if (g == 0 && valid) {
+      double sum = part[0][threadIdx.x];
+#pragma unroll
+      for (int q = 1; q < FG_GROUPS; ++q) sum += part[q][threadIdx.x];
+      Tf[(size_t)d * N + node] = sum;
+    }
+    __syncthreads();
   }
 }
 
-// The same on an nx x ny x nz node grid: six faces per node.
-__global__ void face_grad3d_kernel(const double* __restrict__ mu, const double* __restrict__ u,
-                                   const double* __restrict__ b, const double* __restrict__ eps,
-                                   int nx, int ny, int nz, int B, double* __restrict__ deps) {
-  const int mx = nx - 2, my = ny - 2, mz = nz - 2, n = mx * my * mz;
-  const int N = nx * ny * nz;
+template <int DIMS>
+__global__ void face_combine_kernel(const double* __restrict__ Tf, const double* __restrict__ eps,
+                                    int nx, int ny, int nz, double* __restrict__ deps) {
+  const int nzz = DIMS == 3 ? nz : 1;
+  const int N = nx * ny * nzz;
+  const int plane = nx * ny;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N;
        node += gridDim.x * blockDim.x) {
-    const int j = node % nx, i = (node / nx) % ny, l = node / (nx * ny);
-    const bool in_a = (l > 0 && l < nz - 1 && i > 0 && i < ny - 1 && j > 0 && j < nx - 1);
-    const int pa = in_a ? ((l - 1) * my + (i - 1)) * mx + (j - 1) : -1;
+    const int j = node % nx, i = (node / nx) % ny, l = DIMS == 3 ? node / plane : 0;
     const double ea = eps[node];
     double acc = 0.0;
-    const int dl[6] = {0, 0, 0, 0, -1, 1}, di[6] = {0, 0, -1, 1, 0, 0}, dj[6] = {-1, 1, 0, 0, 0, 0};
-    for (int k = 0; k < 6; ++k) {
-      const int l2 = l + dl[k], i2 = i + di[k], j2 = j + dj[k];
-      if (l2 < 0 || l2 >= nz || i2 < 0 || i2 >= ny || j2 < 0 || j2 >= nx) continue;
-      const bool in_b = (l2 > 0 && l2 < nz - 1 && i2 > 0 && i2 < ny - 1 && j2 > 0 && j2 < nx - 1);
-      if (!in_a && !in_b) continue;
-      const int pb = in_b ? ((l2 - 1) * my + (i2 - 1)) * mx + (j2 - 1) : -1;
-      double T = 0.0;
-      for (int c = 0; c < B; ++c) {
-        const size_t o = (size_t)c * n;
-        const double mua = in_a ? mu[o + pa] : 0.0, mub = in_b ? mu[o + pb] : 0.0;
-        const double ua = in_a ? u[o + pa] : 0.0, ub = in_b ? u[o + pb] : 0.0;
-        const double ba = in_a ? b[o + pa] : 0.0, bb = in_b ? b[o + pb] : 0.0;
-        T += mua * ba + mub * bb - (mua - mub) * (ua - ub);
-      }
-      const double eb = eps[((size_t)l2 * ny + i2) * nx + j2];
+    // faces -x, +x, -y, +y, -z, +z: T_f is stored at the face's lower node
+    const int step[3] = {1, nx, plane};
+    const int coord[3] = {j, i, l}, extent[3] = {nx, ny, nzz};
+#pragma unroll
+    for (int k = 0; k < 2 * DIMS; ++k) {
+      const int d = k >> 1;
+      const bool up = k & 1;
+      if (up ? coord[d] + 1 >= extent[d] : coord[d] == 0) continue;
+      const int other = up ? node + step[d] : node - step[d];
+      const double T = Tf[(size_t)d * N + (up ? node : other)];
+      const double eb = eps[other];
       acc += T * 2.0 * eb * eb / ((ea + eb) * (ea + eb));
     }
     deps[node] += acc;
@@ -553,12 +568,24 @@ pide_status launch_face_grad(pide_ctx* c, const double* mu, const double* u, con
                              int B, double* deps, cudaStream_t st) {
   ProfScope ps(c, st, 3);
   const int N = c->nx * c->ny * c->nz;
-  if (c->dims == 3)
-    face_grad3d_kernel<<<grid_for(N, 128, c->num_sms), 128, 0, st>>>(mu, u, b, c->eps, c->nx,
-                                                                     c->ny, c->nz, B, deps);
-  else
-    face_grad_kernel<<<grid_for(N, 128, c->num_sms), 128, 0, st>>>(mu, u, b, c->eps, c->nx, c->ny,
-                                                                   B, deps);
+  double* Tf = nullptr;
+  PIDE_CUDA_TRY(cudaMallocAsync((void**)&Tf, (size_t)c->dims * N * sizeof(double), st));
+  const dim3 grid((N + 31) / 32), block(32, FG_GROUPS);
+  if (c->dims == 3) {
+    face_t_kernel<3><<<grid, block, 0, st>>>(mu, u, b, c->nx, c->ny, c->nz, B, Tf);
+    face_combine_kernel<3><<<grid_for(N, 256, c->num_sms), 256, 0, st>>>(Tf, c->eps, c->nx, c->ny,
+                                                                        c->nz, deps);
+  } else {
+    face_t_kernel<2><<<grid, block, 0, st>>>(mu, u, b, c->nx, c->ny, 1, B, Tf);
+    face_combine_kernel<2><<<grid_for(N, 256, c->num_sms), 256, 0, st>>>(Tf, c->eps, c->nx, c->ny,
+                                                                        1, deps);
+  }
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(Tf, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("face gradient: ") + cudaGetErrorString(e));
+    return PIDE_ECUDA;
+  }
   PIDE_CUDA_TRY(cudaGetLastError());
   return PIDE_OK;
 }
