@@ -22,13 +22,12 @@
 // barrier, then the pair's collective TMEM release).
 //
 // Schedule: persistent clusters take whole tiles cid, cid + G, ... (G clusters).
-// When the last round would leave most pairs idle (its r tiles at most G / 2),
-// the whole rounds come first and each of the r tiles is then cut into
-// P = G / r ranges of k-blocks, one per cluster; a piece writes its scaled FP32
-// partial tile to a slot of a workspace and a separate reduction kernel adds
-// the P partials of each tile to u in FP64.  At 198^2 unknowns and B = 1024
-// (616 tiles on 76 pairs: 8 rounds and 8 tiles) the ninth round of whole tiles
-// cost as much as a full one.
+// The r tiles of the last, partial round can be cut into P ranges of k-blocks
+// each, dealt round-robin to the clusters (the choice of P is in launch_tc2);
+// a piece writes its scaled FP32 partial tile to a slot of a workspace and a
+// separate reduction kernel adds the P partials of each tile to u.  At 198^2
+// unknowns and B = 1024 (616 tiles on 76 pairs: 8 rounds and 8 tiles) the
+// ninth round of whole tiles cost as much as a full one.
 #include "common.cuh"
 
 namespace pide {
