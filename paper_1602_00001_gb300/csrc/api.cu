@@ -132,10 +132,12 @@ pide_status make_tma_rhs_corr(pide_ctx* c, int bn) {
 // ---------------------------------------------------------------- workspace
 
 pide_status ensure_workspace(pide_ctx* c, int B) {
-  // the SM-pair GEMM's partial tiles: four 256 x 256 FP32 slots per pair (80
-  // MB at 152 SMs), allocated once so that a captured apply allocates nothing
-  if (!c->tail_ws && (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2 ||
-                      c->prec == PIDE_FP16)) {
+  // the SM-pair GEMM's partial tiles (B > 128 only): four 256 x 256 FP32 slots
+  // per pair (80 MB at 152 SMs), allocated once so that a captured apply
+  // allocates nothing
+  if (!c->tail_ws && B > 128 &&
+      (c->prec == PIDE_BF16 || c->prec == PIDE_FP8 || c->prec == PIDE_FP8X2 ||
+       c->prec == PIDE_FP16)) {
     const int slots = 4 * (c->num_sms / 2 > 0 ? c->num_sms / 2 : 1);
     PIDE_CUDA_TRY(cudaMalloc((void**)&c->tail_ws, (size_t)slots * 256 * 256 * sizeof(float)));
     c->tail_slots = slots;
