@@ -324,6 +324,9 @@ pide_status pide_rhs_from_charge(pide_handle h, const double* rho_dev, double* b
  *          no b term, u = 0), chained through the harmonic mean
  *          d eps_f / d eps_a = 2 eps_b^2 / (eps_a + eps_b)^2.
  * u_dev must be the forward solution for b_dev.  db_dev or deps_dev may be NULL.
+ * Scratch (mu, B x n doubles; the face sums, 2 or 3 x nodes doubles) comes from
+ * the stream-ordered allocator (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * The deps sums are deterministic (fixed order, no atomics).
  * Not in the paper: the gradient follows from differentiating L u = b.
  */
 pide_status pide_apply_backward(pide_handle h, const double* gout_dev, const double* u_dev,
