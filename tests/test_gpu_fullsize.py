@@ -67,3 +67,28 @@ def test_fp64_full_size(problem):
     u = s.apply(b[SAMPLE[:2]])
     assert O.rel_error_eq6(u.cpu().numpy(), ref[:2]) < 1e-12
     s.close()
+
+
+def test_fp16_fp8_full_size_b64_and_b4096(problem):
+    """The headline store (FP16 + e4m3 correction, one sweep) at the workload's
+    other batch sizes, on the operator bench.py measures: B = 64 (single-SM
+    tensor-core kernel, stream-K tail) made of the four sampled columns, and
+    B = 4096 (SM pairs: 32 whole rounds, then the last 32 tiles cut along K)
+    made of the 1024 columns at four scales; the sampled columns against the
+    oracle's band-LU solutions."""
+    from paper_1602_00001_gb300.binding import Solver
+    h, eps, b, ref = problem
+    s = Solver(NODES, NODES, h, eps, "fp16_fp8")
+    b64 = np.tile(b[SAMPLE], (16, 1))
+    u64 = s.apply(torch.from_numpy(b64).cuda(), sweeps=1).cpu().numpy()
+    assert O.rel_error_eq6(u64, np.tile(ref, (16, 1))) < 1e-6
+    scales = [1.0, 0.5, -1.0, 2.0]
+    bd = torch.from_numpy(b).cuda()
+    b4k = torch.cat([c * bd for c in scales])
+    with s.profile() as prof:
+        u4k = s.apply(b4k, sweeps=1)
+    assert prof["reduce"][0] > 0, prof
+    cols = [k * BATCH + j for k in range(4) for j in SAMPLE]
+    ref4k = np.concatenate([c * ref for c in scales])
+    assert O.rel_error_eq6(u4k[cols].cpu().numpy(), ref4k) < 1e-6
+    s.close()
