@@ -11,11 +11,12 @@ BF16 + e4m3, FP16, FP16 + e4m3, FP8 hi+lo or FP32.  The e2e figure streams
 steps from pinned host memory through pide_solve_stream (copies in and out
 inside the timed region).  k is the smallest sweep count whose Eq. (6) error
 against the plain FP64 GPU apply is <= 0.5e-6 on sampled columns (checked
-against the FP64 oracle on two columns as well); the sweep count the library
-measured is reported beside it.  The metric is right-hand-side solves per
-second, whole job (all ranks).
+against the FP64 oracle on four columns in the CPU-baseline leg); the sweep
+count the library measured is reported beside it.  The metric is
+right-hand-side solves per second, whole job (all ranks).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --workload batched | adjoint | 3d | formats
 """
 from __future__ import annotations
 
