@@ -63,7 +63,11 @@ def candidates(B: int):
         for sk in (0, 1):
             yield {"gemv_max_b": 1, "gemm_streamk": sk}
     else:
-        for sk, hint in itertools.product([0, 1], [0, 1]):
+        # SM pairs: whole tiles, the K-split last round weighed against its
+        # reduction, or split whenever the round gets shorter; the inverse's
+        # loads with an L2 evict-normal or evict-last hint (evict-first
+        # doubled the pair kernel's DRAM reads)
+        for sk, hint in itertools.product([0, 1, 2], [1, 2]):
             yield {"gemv_max_b": 1, "gemm_2cta": 1, "gemm_bn": 256, "gemm_streamk": sk,
                    "gemm_a_hint": hint}
         for bn, sk in itertools.product([128, 256], [0, 1]):
