@@ -193,3 +193,29 @@ def test_default_weighs_the_reduction(eps):
             mag = s.apply(np.abs(b), sweeps=0)     # L^-1 >= 0: the contraction of |b|
         s.close()
     assert bool(((res[1] - res[2]).abs() <= 1e-4 * mag + 1e-300).all())
+
+
+def test_split_apply_in_cuda_graph(eps):
+    """The refined apply with K-split GEMMs and their reductions, captured once
+    in a CUDA graph and replayed twice, gives the eager result bit for bit (the
+    reduction adds the partials in a fixed order)."""
+    B = 1600
+    b = torch.from_numpy(_b(eps, B, seed=21)).cuda()
+    s = _solver(eps, "fp16_fp8")
+    s.reserve(B)
+    u_eager = s.apply(b, sweeps=1)
+    u = torch.zeros_like(b)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        s.apply(b, u, sweeps=1, stream=st)          # warm-up outside capture
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        s.apply(b, u, sweeps=1, stream=st)
+    for _ in range(2):
+        u.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(u, u_eager)
+    s.close()
