@@ -219,3 +219,24 @@ def test_split_apply_in_cuda_graph(eps):
         torch.cuda.synchronize()
         assert torch.equal(u, u_eager)
     s.close()
+
+
+def test_split_3d_reaches_oracle():
+    """The 3-D operator through split GEMMs: 18 x 18 x 18 nodes (4096 unknowns,
+    16 row slabs, 64 k-blocks), B = 300 (32 tiles of the last round, all
+    split), FP16 + e4m3 with one sweep, against the 3-D oracle."""
+    from oracle import pide_oracle3d as O3
+    from paper_1602_00001_gb300.binding import Solver3D
+    nx = ny = nz = 18
+    rng = np.random.default_rng(5)
+    e3 = np.exp(0.5 * rng.standard_normal((nz, ny, nx)))
+    b = rng.standard_normal((300, 16 ** 3))
+    s = Solver3D(nx, ny, nz, 1.0 / (nx - 1), e3, "fp16_fp8")
+    s.set_tuning(gemm_streamk=2)
+    with s.profile() as prof:
+        u = s.apply(b, sweeps=1).cpu().numpy()
+    assert prof["reduce"][0] >= 2, prof          # the FP16 applies (and the correction GEMM's)
+    cols = [0, 150, 299]
+    ref = O3.solve(nx, ny, nz, e3, b[cols], route="band")
+    assert O.rel_error_eq6(u[cols], ref) < 1e-6
+    s.close()
